@@ -1,0 +1,185 @@
+"""ctypes wrapper over the plain-C slab-hash oracle (slab_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg use it; the product path never imports it. It shares no code
+with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "slab_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NOT_FOUND = 0xFFFFFFFF
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile slab_oracle.c with the host C compiler (portable flags only)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ctype))
+
+
+def load_oracle(path: str | None = None):
+    """Load the oracle library (the in-tree build, or an explicit .so path)."""
+    global _lib
+    with _lock:
+        if path is not None or _lib is None:
+            lib = C.CDLL(path or build_oracle())
+            u32p, u8p, u64p = C.POINTER(C.c_uint32), C.POINTER(C.c_uint8), C.POINTER(C.c_uint64)
+            lib.oracle_create.restype = C.c_void_p
+            lib.oracle_create.argtypes = [C.c_uint32, C.c_int, C.c_uint32, C.c_uint32]
+            lib.oracle_destroy.argtypes = [C.c_void_p]
+            lib.oracle_hash.restype = C.c_uint32
+            lib.oracle_hash.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]
+            lib.oracle_bucket.restype = C.c_uint32
+            lib.oracle_bucket.argtypes = [C.c_void_p, C.c_uint32]
+            lib.oracle_insert.argtypes = [C.c_void_p, u32p, u32p, C.c_uint64, u8p, u64p]
+            lib.oracle_delete.argtypes = [C.c_void_p, u32p, C.c_uint64, u8p, u64p]
+            lib.oracle_search.argtypes = [C.c_void_p, u32p, C.c_uint64, u32p, u8p, u64p]
+            lib.oracle_mixed.argtypes = [C.c_void_p, u8p, u32p, u32p, C.c_uint64, u32p, u8p, u64p]
+            lib.oracle_stats.argtypes = [C.c_void_p, u32p, u32p, u64p]
+            lib.oracle_utilization.restype = C.c_double
+            lib.oracle_utilization.argtypes = [C.c_void_p]
+            lib.oracle_export.restype = C.c_uint64
+            lib.oracle_export.argtypes = [C.c_void_p, u32p, u32p, u32p, C.c_uint64]
+            lib.oracle_check_alloc.restype = C.c_int
+            lib.oracle_check_alloc.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, C.c_uint32, u64p]
+            if path is not None:
+                return lib
+            _lib = lib
+    return _lib
+
+
+def _u32(a):
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+class OracleTable:
+    """A slab hash as its plain definition: B insertion-ordered slot arrays."""
+
+    def __init__(self, num_buckets: int, hash_a: int, hash_b: int, key_only: bool = False,
+                 lib=None):
+        self.lib = lib if lib is not None else load_oracle()
+        self.B = int(num_buckets)
+        self.key_only = bool(key_only)
+        self.h = self.lib.oracle_create(self.B, int(self.key_only), int(hash_a), int(hash_b))
+        if not self.h:
+            raise ValueError("oracle_create rejected its arguments")
+        self.lines = 0
+
+    def close(self):
+        if self.h:
+            self.lib.oracle_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def bucket(self, key: int) -> int:
+        return int(self.lib.oracle_bucket(self.h, int(key)))
+
+    def buckets(self, keys) -> np.ndarray:
+        return np.array([self.lib.oracle_bucket(self.h, int(k)) for k in np.asarray(keys)],
+                        dtype=np.uint32)
+
+    def _count(self):
+        return C.c_uint64(0)
+
+    def insert(self, keys, values=None):
+        keys = _u32(keys)
+        vals = None if values is None else _u32(values)
+        found = np.zeros(len(keys), np.uint8)
+        ln = self._count()
+        self.lib.oracle_insert(self.h, _ptr(keys, C.c_uint32), _ptr(vals, C.c_uint32), len(keys),
+                               _ptr(found, C.c_uint8), C.byref(ln))
+        self.lines += ln.value
+        return found
+
+    def delete(self, keys):
+        keys = _u32(keys)
+        found = np.zeros(len(keys), np.uint8)
+        ln = self._count()
+        self.lib.oracle_delete(self.h, _ptr(keys, C.c_uint32), len(keys), _ptr(found, C.c_uint8),
+                               C.byref(ln))
+        self.lines += ln.value
+        return found
+
+    def search(self, keys):
+        keys = _u32(keys)
+        vals = np.zeros(len(keys), np.uint32)
+        found = np.zeros(len(keys), np.uint8)
+        ln = self._count()
+        self.lib.oracle_search(self.h, _ptr(keys, C.c_uint32), len(keys), _ptr(vals, C.c_uint32),
+                               _ptr(found, C.c_uint8), C.byref(ln))
+        self.lines += ln.value
+        return vals, found
+
+    def mixed(self, ops, keys, values=None):
+        ops = np.ascontiguousarray(ops, dtype=np.uint8)
+        keys = _u32(keys)
+        vals = None if values is None else _u32(values)
+        res = np.zeros(len(keys), np.uint32)
+        found = np.zeros(len(keys), np.uint8)
+        ln = self._count()
+        self.lib.oracle_mixed(self.h, _ptr(ops, C.c_uint8), _ptr(keys, C.c_uint32),
+                              _ptr(vals, C.c_uint32), len(keys), _ptr(res, C.c_uint32),
+                              _ptr(found, C.c_uint8), C.byref(ln))
+        self.lines += ln.value
+        return res, found
+
+    def stats(self):
+        """(slots per bucket, slabs per bucket, {live, slots, slabs, reserved})."""
+        slots = np.zeros(self.B, np.uint32)
+        slabs = np.zeros(self.B, np.uint32)
+        tot = np.zeros(4, np.uint64)
+        self.lib.oracle_stats(self.h, _ptr(slots, C.c_uint32), _ptr(slabs, C.c_uint32),
+                              _ptr(tot, C.c_uint64))
+        return slots, slabs, dict(live=int(tot[0]), slots=int(tot[1]), slabs=int(tot[2]),
+                                  reserved=int(tot[3]))
+
+    def utilization(self) -> float:
+        return float(self.lib.oracle_utilization(self.h))
+
+    def export(self):
+        """Live elements as (bucket, key, value) arrays in bucket / list order."""
+        n = int(self.lib.oracle_export(self.h, None, None, None, 0))
+        b = np.zeros(n, np.uint32)
+        k = np.zeros(n, np.uint32)
+        v = np.zeros(n, np.uint32)
+        self.lib.oracle_export(self.h, _ptr(b, C.c_uint32), _ptr(k, C.c_uint32),
+                               _ptr(v, C.c_uint32), n)
+        return b, k, v
+
+
+def hash_of(a: int, b: int, num_buckets: int, key: int, lib=None) -> int:
+    """h(k; a, b) = ((a k + b) mod p) mod B for one key, no table needed."""
+    lib = lib if lib is not None else load_oracle()
+    return int(lib.oracle_hash(int(a), int(b), int(num_buckets), int(key)))
+
+
+def check_alloc(addrs, bitmaps, num_blocks: int, blocks_per_super: int = 1 << 14, lib=None):
+    """0 if addresses are valid, distinct and exactly match the bitmaps; see the C doc."""
+    lib = lib if lib is not None else load_oracle()
+    addrs = _u32(addrs)
+    bitmaps = _u32(bitmaps)
+    if len(bitmaps) != num_blocks * 32:
+        raise ValueError("bitmap array must hold 32 words per memory block")
+    where = C.c_uint64(0)
+    rc = lib.oracle_check_alloc(_ptr(addrs, C.c_uint32), len(addrs), _ptr(bitmaps, C.c_uint32),
+                                int(num_blocks), int(blocks_per_super), C.byref(where))
+    return int(rc), int(where.value)

@@ -1,0 +1,191 @@
+"""Seeded synthetic inputs shaped like the slab-hash paper's workloads (Sec. 6).
+
+This module is shared by the tests, the benchmark and the oracle's callers. It
+holds no part of the method's arithmetic: no bucket hash, no slab layout, no
+set semantics. It only draws keys, values, op codes and the random hash
+parameters that the method consumes as inputs.
+
+Recipe (Sec. 6.1 and 6.3: uniform random 32-bit keys, no external dataset):
+
+* Distinct keys come from one counter per ``KeyStream``. Counter ``c`` maps to
+  ``pi((c + offset) mod (2^32 - 2))`` where ``pi`` is the bijective 32-bit
+  "lowbias32" integer mixer (two xorshift-multiply rounds, Wellons' hash
+  prospector). Outputs that land on the two reserved sentinels
+  (0xFFFFFFFE, 0xFFFFFFFF) are re-mixed (cycle walking), which keeps the map
+  one-to-one on [0, 2^32 - 3]. Consecutive counter ranges therefore give
+  disjoint key sets: stored keys, absent keys and fresh insert keys never
+  collide by construction.
+* ``value = key XOR 0x9E3779B9``.
+* The universal-hash parameters ``a`` in [1, p-1] and ``b`` in [0, p-1]
+  (Sec. 3.3) are drawn from ``numpy.random.default_rng(seed)`` and handed
+  to both implementations.
+* Search batches mix present keys (a random subset of the stored keys) and
+  absent keys (fresh counters) at a stated hit rate, shuffled.
+* Mixed batches (Sec. 6.3) draw fresh inserts, deletes of distinct live keys,
+  searches of live keys untouched by the batch and searches of absent keys, in
+  stated ratios, shuffled so every op kind can land in one warp. Every key
+  appears in at most one op per batch.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+VALUE_XOR = np.uint32(0x9E3779B9)
+HASH_PRIME = 4294967291  # 2^32 - 5, the largest prime below 2^32
+KEY_LIMIT = 0xFFFFFFFE   # keys must be < this; the two values above are sentinels
+OP_INSERT, OP_DELETE, OP_SEARCH = 0, 1, 2
+
+_M32 = np.uint64(0xFFFFFFFF)
+
+
+def _lowbias32(x: np.ndarray) -> np.ndarray:
+    """Bijective 32-bit mixer (xorshift-multiply, constants 0x7feb352d / 0x846ca68b)."""
+    x = x.astype(np.uint64)
+    x ^= x >> np.uint64(16)
+    x = (x * np.uint64(0x7FEB352D)) & _M32
+    x ^= x >> np.uint64(15)
+    x = (x * np.uint64(0x846CA68B)) & _M32
+    x ^= x >> np.uint64(16)
+    return x
+
+
+def _mix_domain(x: np.ndarray) -> np.ndarray:
+    """Cycle-walk the mixer until every output is a legal key (< 0xFFFFFFFE)."""
+    y = _lowbias32(x)
+    bad = y >= np.uint64(KEY_LIMIT)
+    while bad.any():
+        y[bad] = _lowbias32(y[bad])
+        bad = y >= np.uint64(KEY_LIMIT)
+    return y.astype(np.uint32)
+
+
+class KeyStream:
+    """Hands out disjoint ranges of distinct uniform keys for one seed."""
+
+    def __init__(self, seed: int = 0):
+        self.seed = int(seed)
+        rng = np.random.default_rng([self.seed, 0x5EED])
+        self._offset = int(rng.integers(0, KEY_LIMIT))
+        self._next = 0
+
+    def take(self, n: int) -> np.ndarray:
+        n = int(n)
+        if self._next + n > KEY_LIMIT:
+            raise ValueError("key stream exhausted")
+        c = np.arange(self._next, self._next + n, dtype=np.uint64)
+        self._next += n
+        c = (c + np.uint64(self._offset)) % np.uint64(KEY_LIMIT)
+        return _mix_domain(c)
+
+
+def values_for(keys: np.ndarray) -> np.ndarray:
+    return (np.asarray(keys, dtype=np.uint32) ^ VALUE_XOR).astype(np.uint32)
+
+
+def hash_params(seed: int = 0) -> tuple[int, int]:
+    """Random a in [1, p-1], b in [0, p-1] for h(k) = ((a k + b) mod p) mod B."""
+    rng = np.random.default_rng([int(seed), 0xA11CE])
+    a = int(rng.integers(1, HASH_PRIME))
+    b = int(rng.integers(0, HASH_PRIME))
+    return a, b
+
+
+def buckets_for(n: int, beta: float, per_slab: int = 15) -> int:
+    """B = ceil(n / (M beta)): the bucket count giving a mean of beta slabs per bucket."""
+    return max(1, int(math.ceil(n / (per_slab * beta) - 1e-9)))
+
+
+@dataclass
+class SearchBatch:
+    keys: np.ndarray
+    present: np.ndarray  # bool, True where the key was drawn from the stored set
+
+
+def search_batch(stream: KeyStream, stored: np.ndarray, n: int, hit_rate: float,
+                 rng: np.random.Generator) -> SearchBatch:
+    n_hit = int(round(n * hit_rate))
+    n_hit = min(n_hit, len(stored)) if len(stored) else 0
+    n_miss = n - n_hit
+    hit = stored[rng.choice(len(stored), size=n_hit, replace=False)] if n_hit else \
+        np.empty(0, np.uint32)
+    miss = stream.take(n_miss)
+    keys = np.concatenate([hit, miss]).astype(np.uint32)
+    present = np.concatenate([np.ones(n_hit, bool), np.zeros(n_miss, bool)])
+    perm = rng.permutation(n)
+    return SearchBatch(keys[perm], present[perm])
+
+
+@dataclass
+class MixedBatch:
+    ops: np.ndarray     # uint8 op codes
+    keys: np.ndarray    # uint32
+    values: np.ndarray  # uint32 (inserts: key ^ C; others: 0)
+
+
+def mixed_batch(stream: KeyStream, live: np.ndarray, n: int,
+                ratios: tuple[float, float, float], rng: np.random.Generator,
+                ) -> tuple[MixedBatch, np.ndarray]:
+    """One batch of n mixed ops; returns the batch and the live key set after it."""
+    fi, fd, fs = ratios
+    n_ins = int(round(n * fi))
+    n_del = min(int(round(n * fd)), len(live))
+    n_search = n - n_ins - n_del
+    n_sh = min(n_search // 2, max(0, len(live) - n_del))
+    n_sm = n_search - n_sh
+    pick = rng.choice(len(live), size=n_del + n_sh, replace=False) if len(live) else \
+        np.empty(0, np.int64)
+    dels = live[pick[:n_del]]
+    shit = live[pick[n_del:]]
+    ins = stream.take(n_ins)
+    smiss = stream.take(n_sm)
+    keys = np.concatenate([ins, dels, shit, smiss]).astype(np.uint32)
+    ops = np.concatenate([np.full(n_ins, OP_INSERT, np.uint8), np.full(n_del, OP_DELETE, np.uint8),
+                          np.full(n_sh + n_sm, OP_SEARCH, np.uint8)])
+    vals = np.concatenate([values_for(ins), np.zeros(n - n_ins, np.uint32)]).astype(np.uint32)
+    perm = rng.permutation(n)
+    keep = np.ones(len(live), bool)
+    keep[pick[:n_del]] = False
+    new_live = np.concatenate([live[keep], ins]).astype(np.uint32)
+    return MixedBatch(ops[perm], keys[perm], vals[perm]), new_live
+
+
+@dataclass
+class BulkWorkload:
+    """Sec. 6.1 bulk benchmark: build n pairs, search, delete."""
+    num_buckets: int
+    hash_a: int
+    hash_b: int
+    keys: np.ndarray
+    values: np.ndarray
+    search: SearchBatch
+    delete_keys: np.ndarray
+
+
+def bulk_workload(n: int, beta: float, n_search: int, hit_rate: float, n_delete: int,
+                  seed: int = 0, num_buckets: int | None = None) -> BulkWorkload:
+    stream = KeyStream(seed)
+    rng = np.random.default_rng([int(seed), 0xB01C])
+    keys = stream.take(n)
+    a, b = hash_params(seed)
+    B = num_buckets if num_buckets is not None else buckets_for(n, beta)
+    sb = search_batch(stream, keys, n_search, hit_rate, rng)
+    dels = keys[rng.choice(n, size=min(n_delete, n), replace=False)] if n_delete else \
+        np.empty(0, np.uint32)
+    return BulkWorkload(B, a, b, keys, values_for(keys), sb, dels.astype(np.uint32))
+
+
+def config1(seed: int = 0) -> BulkWorkload:
+    """2^16 pairs into 2^16/(15*0.6) buckets, 2^16 searches at 50 % hit, 2^14 deletes."""
+    return bulk_workload(1 << 16, 0.6, 1 << 16, 0.5, 1 << 14, seed)
+
+
+def config2(beta: float = 0.6, hit_rate: float = 0.5, seed: int = 0) -> BulkWorkload:
+    """2^22 pairs, 2^22 searches at the given hit rate, 2^20 deletes."""
+    return bulk_workload(1 << 22, beta, 1 << 22, hit_rate, 1 << 20, seed)
+
+
+CONFIG3_RATIOS = ((0.5, 0.5, 0.0), (0.2, 0.2, 0.6), (0.05, 0.05, 0.9))
+CONFIG2_BETAS = (0.2, 0.4, 0.6, 0.8, 1.0, 2.0)

@@ -1,0 +1,301 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each ``pin_*`` takes a loaded oracle library and raises AssertionError when the
+oracle disagrees with something other than itself: hand-derived golden values
+(tests/golden/, each with its citation), closed forms, a brute-force flat-set
+model of the Sec. 3.2 operations, invariants, and a statistical law. The same
+pins run against deliberately broken builds of the oracle in
+test_oracle_mutants.py, to show that each plausible mistake is caught.
+"""
+from __future__ import annotations
+
+import os
+import random
+
+import numpy as np
+
+from oracle.oracle import NOT_FOUND, OracleTable, check_alloc, hash_of
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+P = 4294967291
+
+
+def _rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                yield line.split()
+
+
+# --------------------------------------------------------------------------- hash
+def pin_hash_golden(lib):
+    """Sec. 3.3 hash on hand-derived cases (tests/golden/hash_cases.txt)."""
+    for a, b, B, k, want in _rows("hash_cases.txt"):
+        got = hash_of(int(a), int(b), int(B), int(k), lib=lib)
+        assert got == int(want), f"h({k}; a={a}, b={b}) mod {B}: got {got}, want {want}"
+    # a table's bucket() is the same function of its own (a, b, B)
+    t = OracleTable(10, 3, 7, lib=lib)
+    assert [t.bucket(k) for k in (1, 4, P, P + 1)] == [0, 9, 7, 0]
+
+
+def pin_hash_uniform(lib):
+    """Sec. 3.3: a universal hash spreads distinct keys evenly over B buckets.
+
+    With random (a, b) and about 2^16 random distinct keys over B = 512 buckets the bucket
+    counts must pass a chi-square test of uniformity (p-value > 1e-4), and no
+    bucket may be empty. A transposed or dropped operand collapses the spread.
+    """
+    from scipy.stats import chisquare
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        a = int(rng.integers(1, P))
+        b = int(rng.integers(0, P))
+        B = 512
+        t = OracleTable(B, a, b, lib=lib)
+        keys = np.unique(rng.integers(0, 0xFFFFFFFE, size=1 << 16, dtype=np.uint64))
+        cnt = np.bincount(t.buckets(keys), minlength=B)
+        assert cnt.min() > 0
+        assert chisquare(cnt).pvalue > 1e-4, "bucket counts are not uniform"
+
+
+# ------------------------------------------------------------------ set semantics
+def pin_worked_example(lib):
+    """Hand-derived trace of REPLACE / DELETE / SEARCH (tests/golden/worked_example.txt)."""
+    t = OracleTable(1, 1, 0, lib=lib)
+    for row in _rows("worked_example.txt"):
+        if row[0] == "final":
+            _, _, tot = t.stats()
+            assert (tot["live"], tot["slots"], tot["slabs"]) == tuple(map(int, row[1:4])), tot
+            continue
+        op, key, val, _, want_found, want_res, want_lines = row
+        code = {"insert": 0, "delete": 1, "search": 2}[op]
+        before = t.lines
+        res, found = t.mixed(np.array([code], np.uint8), np.array([int(key)], np.uint32),
+                             np.array([int(val)], np.uint32))
+        want_r = NOT_FOUND if want_res == "NF" else int(want_res)
+        assert int(found[0]) == int(want_found), f"{row}: found {found[0]}"
+        assert int(res[0]) == want_r, f"{row}: result {res[0]}"
+        assert t.lines - before == int(want_lines), f"{row}: lines {t.lines - before}"
+
+
+def pin_slab_boundaries(lib):
+    """Slab layout of Sec. 4.2: slot s lies in slab floor(s / 15) (tests/golden/slab_boundaries.txt)."""
+    for n, key, want_lines, want_slabs in _rows("slab_boundaries.txt"):
+        n, key = int(n), int(key)
+        t = OracleTable(1, 1, 0, lib=lib)
+        keys = np.arange(100, 100 + n, dtype=np.uint32)
+        t.insert(keys, keys)
+        q = np.array([key if key >= 0 else 99], np.uint32)
+        before = t.lines
+        t.search(q)
+        assert t.lines - before == int(want_lines), (n, key, t.lines - before)
+        _, slabs, _ = t.stats()
+        assert int(slabs[0]) == int(want_slabs), (n, slabs[0])
+
+
+class FlatSet:
+    """The Sec. 3.2 definitions written over a plain list of pairs, with no buckets."""
+
+    def __init__(self):
+        self.S = []
+
+    def replace(self, k, v):
+        had = any(x == k for x, _ in self.S)
+        self.S = [(x, y) for x, y in self.S if x != k] + [(k, v)]
+        return had
+
+    def delete(self, k):
+        had = any(x == k for x, _ in self.S)
+        self.S = [(x, y) for x, y in self.S if x != k]
+        return had
+
+    def search(self, k):
+        for x, y in self.S:
+            if x == k:
+                return y
+        return None
+
+
+def pin_bruteforce_sequences(lib):
+    """Random op sequences over a tiny key universe agree with the flat-set model.
+
+    B in {1, 2, 3} and 10 keys force collisions, replaces of present keys,
+    deletes of absent keys and re-inserts after deletes.
+    """
+    rnd = random.Random(1234)
+    for trial in range(60):
+        B = 1 + trial % 3
+        a, b = rnd.randrange(1, P), rnd.randrange(0, P)
+        t = OracleTable(B, a, b, lib=lib)
+        ref = FlatSet()
+        new_inserts = deletes_hit = 0
+        for _ in range(120):
+            op = rnd.randrange(3)
+            k = rnd.randrange(10) * 7919
+            v = rnd.randrange(1 << 32)
+            res, found = t.mixed(np.array([op], np.uint8), np.array([k], np.uint32),
+                                 np.array([v], np.uint32))
+            if op == 0:
+                had = ref.replace(k, v)
+                assert int(found[0]) == int(had) and int(res[0]) == int(not had)
+                new_inserts += not had
+            elif op == 1:
+                had = ref.delete(k)
+                assert int(found[0]) == int(had) and int(res[0]) == int(had)
+                deletes_hit += had
+            else:
+                want = ref.search(k)
+                assert int(found[0]) == int(want is not None)
+                assert int(res[0]) == (NOT_FOUND if want is None else want)
+        _, _, tot = t.stats()
+        assert tot["live"] == len(ref.S) == new_inserts - deletes_hit
+        assert tot["slots"] == new_inserts, "tombstones must not be reused"
+        bk, keys, vals = t.export()
+        assert sorted(zip(keys.tolist(), vals.tolist())) == sorted(ref.S)
+        for bb, kk in zip(bk.tolist(), keys.tolist()):
+            assert bb == t.bucket(kk)
+
+
+def pin_batch_forms_agree(lib):
+    """insert/delete/search batches give what the same ops give one at a time."""
+    rng = np.random.default_rng(3)
+    keys = rng.choice(1 << 20, size=3000, replace=False).astype(np.uint32)
+    vals = rng.integers(0, 1 << 32, size=3000, dtype=np.uint64).astype(np.uint32)
+    t1 = OracleTable(97, 5, 11, lib=lib)
+    t2 = OracleTable(97, 5, 11, lib=lib)
+    f1 = t1.insert(keys, vals)
+    r2, f2 = t2.mixed(np.zeros(3000, np.uint8), keys, vals)
+    assert (f1 == 0).all() and (f2 == 0).all() and (r2 == 1).all()
+    d1 = t1.delete(keys[::3])
+    r2, d2 = t2.mixed(np.ones(1000, np.uint8), keys[::3], None)
+    assert (d1 == 1).all() and (d2 == 1).all() and (r2 == 1).all()
+    v1, s1 = t1.search(keys)
+    v2, s2 = t2.mixed(np.full(3000, 2, np.uint8), keys, None)
+    want_found = np.ones(3000, np.uint8)
+    want_found[::3] = 0
+    assert (s1 == want_found).all() and (s2 == want_found).all()
+    want_v = np.where(want_found == 1, vals, np.uint32(NOT_FOUND))
+    assert (v1 == want_v).all() and (v2 == want_v).all()
+
+
+def pin_invariants(lib):
+    """Every live key is found with its latest value; deleted and absent keys are
+    not; live = new inserts - deletes that hit; used slots = new inserts."""
+    rng = np.random.default_rng(11)
+    pool = rng.choice(1 << 31, size=20000, replace=False).astype(np.uint32)
+    stored, absent = pool[:12000], pool[12000:]
+    t = OracleTable(400, 123456789, 987654321, lib=lib)
+    f = t.insert(stored, stored ^ np.uint32(0x9E3779B9))
+    assert f.sum() == 0
+    f = t.insert(stored[:3000], stored[:3000] + np.uint32(1))  # replaces
+    assert f.sum() == 3000
+    d = t.delete(stored[5000:9000])
+    assert d.sum() == 4000
+    d = t.delete(absent[:1000])
+    assert d.sum() == 0
+    v, found = t.search(stored)
+    live = np.ones(12000, bool)
+    live[5000:9000] = False
+    assert (found.astype(bool) == live).all()
+    want = stored ^ np.uint32(0x9E3779B9)
+    want[:3000] = stored[:3000] + np.uint32(1)
+    assert (v[live] == want[live]).all()
+    assert (v[~live] == NOT_FOUND).all()
+    v, found = t.search(absent)
+    assert found.sum() == 0 and (v == NOT_FOUND).all()
+    _, _, tot = t.stats()
+    assert tot["live"] == 12000 - 4000
+    assert tot["slots"] == 12000
+
+
+def pin_reserved_keys(lib):
+    """The two sentinel keys (Sec. 3.2 footnote) are refused, not stored."""
+    t = OracleTable(8, 3, 4, lib=lib)
+    keys = np.array([1, 0xFFFFFFFE, 2, 0xFFFFFFFF], np.uint32)
+    f = t.insert(keys, keys)
+    assert f.tolist() == [0, 0, 0, 0]
+    _, _, tot = t.stats()
+    assert tot["live"] == 2 and tot["reserved"] == 2
+    v, found = t.search(keys)
+    assert found.tolist() == [1, 0, 1, 0]
+    assert v[1] == NOT_FOUND and v[3] == NOT_FOUND
+
+
+# ------------------------------------------------------------- slab bookkeeping
+def pin_slab_count_closed_form(lib):
+    """A bucket with s used slots has max(1, ceil(s / M)) slabs (M = 15 pairs or
+    30 keys, Sec. 4.2); the lines of n sequential new inserts into one bucket sum
+    to sum_{i<n} (floor(i / M) + 1)."""
+    for key_only, M in ((False, 15), (True, 30)):
+        for n in (0, 1, 14, 15, 16, 29, 30, 31, 44, 45, 46, 100, 451):
+            t = OracleTable(1, 1, 0, key_only=key_only, lib=lib)
+            keys = np.arange(1, n + 1, dtype=np.uint32)
+            t.insert(keys, keys)
+            slots, slabs, _ = t.stats()
+            assert int(slots[0]) == n
+            assert int(slabs[0]) == max(1, -(-n // M)), (key_only, n, slabs[0])
+            assert t.lines == sum(i // M + 1 for i in range(n)), (key_only, n, t.lines)
+
+
+def pin_max_utilization(lib):
+    """Sec. 4.2 / Sec. 6.1: a single full bucket reaches the maximum utilization
+    M x / (M x + y) = 120 / 128 (the paper's "94%"), in both modes."""
+    for key_only, M in ((False, 15), (True, 30)):
+        t = OracleTable(1, 1, 0, key_only=key_only, lib=lib)
+        keys = np.arange(1, 15 * M + 1, dtype=np.uint32)
+        t.insert(keys, keys)
+        assert abs(t.utilization() - 120.0 / 128.0) < 1e-12, t.utilization()
+        assert round(100 * t.utilization()) == 94
+
+
+def pin_mean_slabs_binomial(lib):
+    """Sec. 3.3: keys spread uniformly, so a bucket's load is Binomial(n, 1/B) and
+    its expected slab count is E[max(1, ceil(X / 15))]. At n = 2^16 the oracle's
+    mean slabs per bucket must match that expectation within 2 %, for every
+    beta the bulk benchmark sweeps (B = ceil(n / (15 beta)))."""
+    from scipy.stats import binom
+    rng = np.random.default_rng(5)
+    n = 1 << 16
+    keys = np.unique(rng.integers(0, 0xFFFFFFFE, size=n, dtype=np.uint64)).astype(np.uint32)
+    n = len(keys)
+    for beta in (0.2, 0.6, 1.0, 2.0):
+        B = int(np.ceil(n / (15 * beta)))
+        t = OracleTable(B, int(rng.integers(1, P)), int(rng.integers(0, P)), lib=lib)
+        t.insert(keys, keys)
+        _, slabs, tot = t.stats()
+        x = np.arange(0, 15 * 40)
+        pmf = binom.pmf(x, n, 1.0 / B)
+        expect = float((pmf * np.maximum(1, -(-x // 15))).sum())
+        got = tot["slabs"] / B
+        assert abs(got - expect) / expect < 0.02, (beta, got, expect)
+
+
+# ------------------------------------------------------------------- SlabAlloc
+def pin_alloc_check(lib):
+    """Sec. 5 address layout (unit bits [0,10), memory block [10,24), super block
+    [24,32)) and bitmap ownership (word w of a block covers units 32w..32w+31),
+    on hand-built cases."""
+    nb = 4
+    bm = np.zeros(nb * 32, np.uint32)
+    # block 0: units 0, 1 (word 0 bits 0-1) and unit 1023 (word 31, bit 31)
+    bm[0] = 0b11
+    bm[31] = 1 << 31
+    # block 1, unit 37: word 32 + 1, bit 5
+    bm[33] = 1 << 5
+    # with 2 blocks per super block, super block 1 / block 1 is linear block 3, unit 64: word 96 + 2
+    bm[98] = 1
+    addrs = np.array([0, 1, 1023, (1 << 10) | 37, (1 << 24) | (1 << 10) | 64], np.uint32)
+    assert check_alloc(addrs, bm, nb, blocks_per_super=2, lib=lib) == (0, 0)
+    dup = np.array([0, 1, 1023, (1 << 10) | 37, (1 << 24) | (1 << 10) | 64, 1], np.uint32)
+    assert check_alloc(dup, bm, nb, blocks_per_super=2, lib=lib)[0] == 2
+    bad = np.array([(2 << 10) | 5], np.uint32)  # block field 2 >= 2 blocks per super block
+    assert check_alloc(bad, np.zeros(nb * 32, np.uint32), nb, blocks_per_super=2, lib=lib)[0] == 1
+    far = np.array([(2 << 24) | 5], np.uint32)  # super block 2 -> linear block 4 >= 4 blocks
+    assert check_alloc(far, np.zeros(nb * 32, np.uint32), nb, blocks_per_super=2, lib=lib)[0] == 1
+    bm2 = bm.copy()
+    bm2[0] = 0b111
+    assert check_alloc(addrs, bm2, nb, blocks_per_super=2, lib=lib) == (3, 0)
+
+
+ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
