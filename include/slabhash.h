@@ -1,0 +1,259 @@
+/*
+ * slabhash.h - C ABI of libslabhash.so, a GB300 (sm_103a) implementation of the
+ * slab hash: a dynamic GPU hash table with chaining whose lists are slab lists
+ * served by warp-cooperative work sharing (WCWS), with SlabAlloc extending the
+ * lists (Ashkiani, Farach-Colton, Owens, "A Dynamic Hash Table for the GPU",
+ * arXiv 1710.11246).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named d_* are CUDA device pointers on the device that was current
+ *   when the table was created. Pointers named h_* are host pointers. The caller
+ *   owns every batch array and keeps it alive until the work queued on `stream`
+ *   has completed. The table owns its slabs, pool, bitmaps and counters.
+ * - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *   stream. Batch calls are asynchronous: they queue kernels and return.
+ * - Return value: SLAB_OK, or an error code for bad arguments (nothing queued)
+ *   and for CUDA launch or copy failures. Errors that happen on the device
+ *   while a batch runs (a sentinel key, an exhausted pool, an iteration cap
+ *   reached) do not stop the batch; they set bits in the table's device status
+ *   word, read and cleared by slab_status().
+ * - Keys are uint32 in [0, 2^32 - 3]. 0xFFFFFFFF marks an empty slot and
+ *   0xFFFFFFFE a deleted one (Sec. 3.2, footnote on the two reserved key
+ *   values); an op on either is skipped and reported as SLAB_FLAG_RESERVED_KEY.
+ * - Batch results are defined when each key appears in at most one op of a
+ *   batch. Ops of one batch are concurrent (Sec. 6.3): with repeated keys every
+ *   outcome is one of the serial orders of those ops.
+ * - A table handle is not thread-safe: issue its calls from one host thread.
+ */
+#ifndef SLABHASH_H
+#define SLABHASH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slab_table slab_table; /* opaque, library-owned */
+
+/* Element types (Sec. 4.2 "Choice of parameters"): 64-bit key-value pairs, 15 per
+ * 128-byte slab (even lanes keys, odd lanes values), or 32-bit keys, 30 per slab. */
+enum slab_mode { SLAB_MODE_KEY_VALUE = 0, SLAB_MODE_KEY_ONLY = 1 };
+
+/* uint8 op codes of a mixed batch (Sec. 6.3 concurrent benchmark). */
+enum slab_op { SLAB_OP_INSERT = 0, SLAB_OP_DELETE = 1, SLAB_OP_SEARCH = 2 };
+
+enum slab_rc {
+    SLAB_OK = 0,
+    SLAB_ERR_INVALID_ARG = 1,
+    SLAB_ERR_RESERVED_KEY = 2, /* a batch held a sentinel key */
+    SLAB_ERR_OUT_OF_SLABS = 3, /* SlabAlloc found no free slab */
+    SLAB_ERR_ITER_LIMIT = 4,   /* an op hit the per-op iteration cap */
+    SLAB_ERR_CUDA = 5,
+    SLAB_ERR_CORRUPT = 6       /* a list held a next pointer outside the pool */
+};
+
+/* Bits of the device status word (see slab_status). */
+#define SLAB_FLAG_RESERVED_KEY 0x1u
+#define SLAB_FLAG_OUT_OF_SLABS 0x2u
+#define SLAB_FLAG_ITER_LIMIT 0x4u
+#define SLAB_FLAG_BAD_POINTER 0x8u /* an op met a next pointer outside the pool and stopped */
+
+#define SLAB_EMPTY_KEY 0xFFFFFFFFu     /* empty slot; also the empty next pointer */
+#define SLAB_TOMBSTONE_KEY 0xFFFFFFFEu /* deleted slot */
+#define SLAB_NOT_FOUND 0xFFFFFFFFu     /* search result for a missing key */
+#define SLAB_HASH_PRIME 4294967291u    /* p = 2^32 - 5 in h(k) = ((a k + b) mod p) mod B */
+
+/* Kernel families (see slab_config). */
+enum slab_variant {
+    SLAB_VARIANT_STAGED = 0, /* default: per-warp op window, slabs staged in shared memory */
+    SLAB_VARIANT_DIRECT = 1  /* the Fig. "alg:search" loop: one op per lane, global reads */
+};
+
+/* Launch and safety parameters of one table. */
+typedef struct slab_config {
+    int32_t variant;           /* enum slab_variant */
+    int32_t threads_per_block; /* multiple of 32, 32..1024 */
+    int32_t blocks_per_sm;     /* resident blocks per SM used to size the persistent grid; 0 = occupancy maximum */
+    uint32_t iter_limit;       /* cap on slab reads and retries of one op; reaching it ends the op with SLAB_FLAG_ITER_LIMIT */
+    uint32_t random_probes;    /* SlabAlloc resident changes drawn by hash before a linear sweep of all blocks */
+} slab_config;
+
+/* Geometry of one table (read-only). */
+typedef struct slab_info {
+    uint32_t num_buckets;        /* B: base slabs */
+    int32_t mode;                /* enum slab_mode */
+    uint32_t elements_per_slab;  /* M: 15 or 30 */
+    uint32_t hash_a, hash_b;     /* universal hash parameters */
+    uint64_t pool_slabs;         /* SlabAlloc memory units (multiple of 1024) */
+    uint32_t num_memory_blocks;  /* pool_slabs / 1024 */
+    uint32_t blocks_per_super;   /* memory blocks per super block in the 32-bit address (2^14) */
+    uint32_t num_super_blocks;   /* ceil(num_memory_blocks / blocks_per_super) */
+    uint32_t sm_count;
+    uint64_t device_bytes;       /* bytes the table holds on the device */
+} slab_info;
+
+/*
+ * Create an empty slab hash with B = num_buckets base slabs (Sec. 3.3, a
+ * direct-address table of B slab lists) and a SlabAlloc pool of `pool_slabs`
+ * 128-byte memory units (Sec. 5), rounded up to whole memory blocks of 1024
+ * units. hash_a in [1, p-1] and hash_b in [0, p-1] are the random parameters
+ * of h(k; a, b) = ((a k + b) mod p) mod B, p = 2^32 - 5 (Sec. 3.3); the caller
+ * draws them. All super blocks sit in one contiguous allocation (the
+ * "SlabAlloc-light" layout of Sec. 5, used in the paper's experiments, Sec. 6),
+ * so a 32-bit slab address decodes with one multiply-add.
+ * Errors: SLAB_ERR_INVALID_ARG for num_buckets = 0, a bad mode, a or b out of
+ * range, pool_slabs = 0, or more than 2^32 - 2 slabs in total; SLAB_ERR_CUDA
+ * if device memory cannot be allocated. On success *out owns device memory
+ * until slab_destroy. The table starts empty (as after slab_reset).
+ */
+int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b,
+                uint64_t pool_slabs, slab_table **out);
+
+/* Free the table's device memory. Waits for the device first. NULL is a no-op. */
+void slab_destroy(slab_table *t);
+
+/* Empty the table: every slot and next pointer EMPTY, every SlabAlloc bitmap
+ * bit clear, status word zero. One fill kernel on `stream`. */
+int slab_reset(slab_table *t, void *stream);
+
+/* Geometry of the table. */
+int slab_get_info(const slab_table *t, slab_info *out);
+
+/* Current launch parameters; and replacing them (validated; SLAB_ERR_INVALID_ARG
+ * leaves the old ones). */
+int slab_get_config(const slab_table *t, slab_config *out);
+int slab_set_config(slab_table *t, const slab_config *cfg);
+
+/*
+ * Bulk build / incremental insertion: REPLACE(k, v) for each of the n pairs
+ * (Sec. 3.2 "Insertion", Sec. 4.3.2): if k is present its value is replaced,
+ * otherwise the pair takes the first empty slot of its list, and a full list
+ * grows by one SlabAlloc slab linked by a 32-bit CAS on the tail's next
+ * pointer. Deleted slots are not reused, so keys stay unique (Sec. 3.2).
+ * d_keys, d_values: n uint32 each (d_values ignored in key-only mode, may be
+ * NULL there). d_found (nullable): n bytes, 1 if the key was already present
+ * (its value replaced), else 0.
+ */
+int slab_insert_batch(slab_table *t, const uint32_t *d_keys, const uint32_t *d_values,
+                      uint8_t *d_found, uint32_t n, void *stream);
+
+/*
+ * DELETE(k) for each of the n keys (Sec. 3.2 "Deletion", Sec. 4.3.3): the slot
+ * holding k gets the tombstone key; a missing key is not an error.
+ * d_found (nullable): n bytes, 1 if k was present and deleted, else 0.
+ */
+int slab_delete_batch(slab_table *t, const uint32_t *d_keys, uint8_t *d_found, uint32_t n,
+                      void *stream);
+
+/*
+ * SEARCH(k) for each of the n keys (Sec. 3.2 "Search", Sec. 4.3.1): the value
+ * stored with k, or SLAB_NOT_FOUND. In key-only mode the value is 0 on a hit.
+ * d_values_out: n uint32. d_found (nullable): n bytes, 1 on a hit; it tells a
+ * stored value 0xFFFFFFFF apart from a miss. The table is read-only during the
+ * batch, so slab reads may use the non-coherent cache path.
+ */
+int slab_search_batch(slab_table *t, const uint32_t *d_keys, uint32_t *d_values_out,
+                      uint8_t *d_found, uint32_t n, void *stream);
+
+/*
+ * Concurrent batch (Sec. 6.3): op i is d_ops[i] (enum slab_op) on d_keys[i]
+ * with d_values[i] (inserts only; may be NULL in key-only mode). One kernel
+ * serves all three kinds; any mix can share a warp. d_results[i]:
+ *   search -> the value or SLAB_NOT_FOUND (0 on a key-only hit);
+ *   insert -> 1 if the key was new, 0 if an existing value was replaced;
+ *   delete -> 1 if the key was deleted, 0 if it was absent.
+ * d_found (nullable): 1 iff the key was present when op i took effect.
+ * An op code > 2 is skipped (result 0).
+ */
+int slab_mixed_batch(slab_table *t, const uint8_t *d_ops, const uint32_t *d_keys,
+                     const uint32_t *d_values, uint32_t *d_results, uint8_t *d_found,
+                     uint32_t n, void *stream);
+
+/*
+ * Synchronize `stream`, then read and clear the device status word.
+ * *h_flags (nullable) receives the SLAB_FLAG_* bits that were set. Returns
+ * SLAB_OK if none were set, else the most serious of SLAB_ERR_CORRUPT,
+ * SLAB_ERR_OUT_OF_SLABS, SLAB_ERR_ITER_LIMIT, SLAB_ERR_RESERVED_KEY, in that
+ * order.
+ */
+int slab_status(slab_table *t, void *stream, uint32_t *h_flags);
+
+/*
+ * Chain statistics, one warp per bucket. d_slots (nullable): B uint32, used
+ * slots of each list (live plus tombstones). d_slabs (nullable): B uint32,
+ * slabs of each list (base slab included). h_totals (nullable): 6 uint64 =
+ * {live elements, used slots, slabs, pool slabs marked allocated in the
+ * bitmaps, lists whose used slots are not a prefix in (slab, lane) order,
+ * slabs linked from a list}. Memory utilization (Sec. 3.3) is
+ * (x / 128) * live / slabs with x = 8 (pairs) or 4 (keys). Synchronizes
+ * `stream` when h_totals is given.
+ */
+int slab_stats(slab_table *t, uint32_t *d_slots, uint32_t *d_slabs, uint64_t *h_totals,
+               void *stream);
+
+/*
+ * Every live element as (bucket, key, value), compacted in no particular
+ * order. At most `capacity` are written; *h_count receives the number of live
+ * elements (which may exceed capacity). d_buckets and d_values are nullable.
+ * Synchronizes `stream`.
+ */
+int slab_export(slab_table *t, uint32_t *d_buckets, uint32_t *d_keys, uint32_t *d_values,
+                uint64_t capacity, uint64_t *h_count, void *stream);
+
+/* h(k) for n keys (Sec. 3.3), as the batch kernels compute it. d_buckets_out: n uint32. */
+int slab_bucket_of(slab_table *t, const uint32_t *d_keys, uint32_t *d_buckets_out, uint32_t n,
+                   void *stream);
+
+/*
+ * SlabAlloc allocation microbenchmark (Sec. 5: one 128-byte slab allocation
+ * per thread). n requests, one per lane; each warp serves its lanes' requests
+ * one at a time with warp_allocate (ballot over the resident block's register
+ * bitmaps, one atomic on the owning bitmap word, resident change by hash when
+ * full). d_addrs_out: n uint32 slab addresses (unit bits [0,10), memory block
+ * [10,24), super block [24,32)), or SLAB_EMPTY_KEY where the pool was
+ * exhausted (and SLAB_FLAG_OUT_OF_SLABS set). The slabs are not linked into
+ * any list; free them with slab_free_batch or slab_reset.
+ */
+int slab_alloc_batch(slab_table *t, uint32_t *d_addrs_out, uint32_t n, void *stream);
+
+/* SlabAlloc deallocation (Sec. 5): clear the bitmap bit of each of n slab
+ * addresses (SLAB_EMPTY_KEY entries are skipped). The slabs must hold only
+ * empty slots, as slabs from slab_alloc_batch do. */
+int slab_free_batch(slab_table *t, const uint32_t *d_addrs, uint32_t n, void *stream);
+
+/* Copy the SlabAlloc bitmaps (32 uint32 words per memory block, bit u%32 of
+ * word u/32 set iff unit u of that block is allocated) to d_dst. n_words must
+ * equal 32 * num_memory_blocks. */
+int slab_copy_bitmaps(const slab_table *t, uint32_t *d_dst, uint64_t n_words, void *stream);
+
+/* Human-readable name of a return code. Never NULL. */
+const char *slab_error_string(int rc);
+
+/*
+ * Roofline probes (measurement only; no table involved).
+ *
+ * slab_probe_random_lines: n_reads reads of whole 128-byte lines at uniformly
+ * random line indices in [0, footprint_lines) of d_buf, one line per warp
+ * access (32 lanes x 4 bytes), `lines_in_flight` independent lines per warp.
+ * The xor of all words read lands in *d_sink (one uint32) so the reads cannot
+ * be elided. d_buf must hold footprint_lines * 32 uint32.
+ *
+ * slab_probe_random_cas: n_ops 64-bit atomicCAS operations, each on one of
+ * the 15 pair slots of a random line in [0, footprint_lines) of d_buf (which
+ * holds footprint_lines * 16 uint64), expecting 0 and writing a nonzero value,
+ * `ops_in_flight` independent CASes per thread. With d_buf zeroed and far more
+ * slots than n_ops most CASes succeed, like an insert claiming an empty pair.
+ */
+int slab_probe_random_lines(const uint32_t *d_buf, uint64_t footprint_lines, uint64_t n_reads,
+                            uint32_t seed, int lines_in_flight, int threads_per_block,
+                            uint32_t *d_sink, void *stream);
+int slab_probe_random_cas(unsigned long long *d_buf, uint64_t footprint_lines, uint64_t n_ops,
+                          uint32_t seed, int ops_in_flight, int threads_per_block, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLABHASH_H */

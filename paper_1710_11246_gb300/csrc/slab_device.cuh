@@ -1,0 +1,186 @@
+// Device-side building blocks of the slab hash: slab layout, universal hash,
+// coherent loads, and SlabAlloc (Sec. 5). Included by the kernel translation
+// units only.
+#pragma once
+#include <cstdint>
+
+namespace slab {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;   // empty slot and empty next pointer
+constexpr uint32_t kTombstone = 0xFFFFFFFEu;  // deleted slot
+constexpr uint32_t kNotFound = 0xFFFFFFFFu;
+constexpr uint32_t kPrime = 4294967291u;      // 2^32 - 5
+constexpr int kAddressLane = 31;              // lane holding the next pointer (Sec. 4.2)
+constexpr uint32_t kWordsPerSlab = 32;        // 128-byte slab, one word per lane
+constexpr uint32_t kUnitsPerBlock = 1024;     // memory units per memory block (Sec. 5)
+constexpr uint32_t kBlocksPerSuper = 1u << 14;
+
+// Key lanes of a slab: even lanes 0..28 for 15 pairs, lanes 0..29 for 30 keys.
+constexpr uint32_t kKeyLanesKV = 0x15555555u;
+constexpr uint32_t kKeyLanesKeyOnly = 0x3FFFFFFFu;
+
+enum : uint32_t { kFlagReserved = 1u, kFlagOutOfSlabs = 2u, kFlagIterLimit = 4u, kFlagBadPointer = 8u };
+enum : uint8_t { kOpInsert = 0, kOpDelete = 1, kOpSearch = 2 };
+// Kernel families by the ops they serve.
+enum : int { kKindSearch = 0, kKindInsert = 1, kKindDelete = 2, kKindMixed = 3 };
+
+struct TableView {
+    uint32_t* slabs;      // B base slabs, then the SlabAlloc pool
+    uint32_t* pool;       // slabs + B * 32: unit `a` of the pool at pool + a * 32
+    uint32_t* bitmaps;    // 32 words per memory block
+    uint32_t* status;     // device status word (kFlag*)
+    uint64_t fastmod_m;   // ceil(2^64 / B) for the bucket reduction
+    uint32_t num_buckets;
+    uint32_t hash_a, hash_b;
+    uint32_t num_blocks;  // memory blocks in the pool
+    uint32_t pool_units;  // num_blocks * 1024: every valid pool address is below this
+    uint32_t iter_limit;
+    uint32_t random_probes;
+    uint32_t epoch;       // distinct per launch; spreads resident blocks over launches
+};
+
+struct BatchArgs {
+    const uint8_t* ops;
+    const uint32_t* keys;
+    const uint32_t* values;
+    uint32_t* results;
+    uint8_t* found;
+    uint32_t n;
+};
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// h(k; a, b) = ((a k + b) mod p) mod B (Sec. 3.3). a k + b < 2^64 since a, b < p.
+// mod p folds the high word with 2^32 = 5 (mod p) twice; mod B is Lemire, Kaser
+// and Kurz's direct remainder ("Faster remainder by direct computation", 2019):
+// with m = ceil(2^64 / B), n mod B = floor(((m n) mod 2^64) * B / 2^64) for
+// every 32-bit n and B.
+__device__ __forceinline__ uint32_t bucket_of(const TableView& T, uint32_t k) {
+    uint64_t x = (uint64_t)T.hash_a * k + T.hash_b;
+    uint64_t t = (x >> 32) * 5ull + (x & 0xFFFFFFFFull);  // < 6 * 2^32
+    t = (t >> 32) * 5ull + (t & 0xFFFFFFFFull);           // < 2^32 + 30
+    uint32_t r = (uint32_t)(t >= kPrime ? t - kPrime : t);
+    uint64_t low = T.fastmod_m * r;
+    return (uint32_t)__umul64hi(low, (uint64_t)T.num_buckets);
+}
+
+// Slab word reads. Mutating kernels read through L2 with relaxed gpu-scope
+// loads so that a re-read after a failed CAS sees other warps' writes; the
+// search-only kernel may use the non-coherent path because nothing writes the
+// table while it runs.
+__device__ __forceinline__ uint32_t ld_coherent(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_readonly(const uint32_t* p) { return __ldg(p); }
+
+template <bool kReadOnly>
+__device__ __forceinline__ uint32_t ld_slab(const uint32_t* p) {
+    if constexpr (kReadOnly) return ld_readonly(p);
+    else return ld_coherent(p);
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Streaming loads for the op arrays: each element is read once, so mark it
+// evict-first (ld.global.cs) and keep it from displacing table lines in L2.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ uint32_t ld_stream_u8(const uint8_t* p) { return __ldcs(p); }
+
+__device__ __forceinline__ void set_flag(const TableView& T, uint32_t f) { atomicOr(T.status, f); }
+
+// A next pointer read from a slab must name a pool unit; anything else means the
+// table was overwritten from outside, and the op stops instead of reading out of
+// bounds.
+__device__ __forceinline__ bool valid_next(const TableView& T, uint32_t a) { return a < T.pool_units; }
+
+__device__ __forceinline__ uint32_t* slab_ptr(const TableView& T, uint32_t bucket, uint32_t cur) {
+    // cur == kEmptyKey means "the base slab of `bucket`", otherwise a pool address.
+    // SlabAlloc-light decode (Sec. 5): the pool is contiguous and the 32-bit
+    // address is the linear unit index (super block * 2^14 + block) * 1024 + unit.
+    return cur == kEmptyKey ? T.slabs + (uint64_t)bucket * kWordsPerSlab
+                            : T.pool + (uint64_t)cur * kWordsPerSlab;
+}
+
+// --------------------------------------------------------------------------
+// SlabAlloc (Sec. 5). Each warp owns a resident memory block; lane i keeps word i
+// of its bitmap (units 32i..32i+31) in a register. An allocation ballots the
+// lanes with a free bit, the lowest such lane claims its lowest free bit with one
+// atomic on the global bitmap word and the address is broadcast by shuffle. When
+// the block looks full the warp moves to another block chosen by hashing its
+// global warp id with its count of resident changes; the new block's 32 bitmap
+// words arrive in one coalesced 128-byte read.
+// --------------------------------------------------------------------------
+struct AllocCtx {
+    uint32_t block;    // resident memory block, or kNoBlock (warp-uniform)
+    uint32_t bitmap;   // this lane's word of the resident block's bitmap
+    uint32_t changes;  // resident changes so far (warp-uniform)
+};
+constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
+constexpr uint32_t kAllocFailed = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    // murmur3 finalizer
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t resident_block(const TableView& T, uint32_t warp_gid,
+                                                   uint32_t attempt) {
+    // First `random_probes` changes: a hash of (warp id, attempt, launch epoch).
+    // After that a sweep of every block from a hashed start, so that a pool with
+    // any free unit left is always found before the allocation gives up.
+    uint32_t seed = mix32(warp_gid * 0x9E3779B1u + T.epoch * 0x7F4A7C15u);
+    if (attempt < T.random_probes) return mix32(seed ^ (attempt * 0x632BE5ABu)) % T.num_blocks;
+    // start < num_blocks and the offset < num_blocks < 2^22: no wrap-around.
+    return (seed % T.num_blocks + (attempt - T.random_probes)) % T.num_blocks;
+}
+
+// Returns a pool address, or kAllocFailed once every block has been probed.
+// Must be called by all 32 lanes with warp-uniform control flow.
+__device__ __forceinline__ uint32_t warp_allocate(const TableView& T, AllocCtx& c, uint32_t warp_gid) {
+    const uint32_t lane = lane_id();
+    const uint32_t max_changes = T.random_probes + T.num_blocks;
+    for (;;) {
+        if (c.block == kNoBlock) {
+            if (c.changes >= max_changes) return kAllocFailed;
+            c.block = resident_block(T, warp_gid, c.changes);
+            c.changes++;
+            c.bitmap = ld_coherent(T.bitmaps + (uint64_t)c.block * 32 + lane);
+        }
+        uint32_t free_lanes = __ballot_sync(kFull, c.bitmap != 0xFFFFFFFFu);
+        if (free_lanes == 0) {
+            c.block = kNoBlock;
+            continue;
+        }
+        int src = __ffs(free_lanes) - 1;
+        uint32_t addr = 0, ok = 0;
+        if ((int)lane == src) {
+            uint32_t bit = (uint32_t)(__ffs(~c.bitmap) - 1);
+            uint32_t mask = 1u << bit;
+            uint32_t old = atomicOr(T.bitmaps + (uint64_t)c.block * 32 + lane, mask);
+            c.bitmap = old | mask;  // refresh from what the atomic saw
+            ok = (old & mask) == 0;
+            addr = (c.block << 10) | (lane << 5) | bit;
+        }
+        ok = __shfl_sync(kFull, ok, src);
+        addr = __shfl_sync(kFull, addr, src);
+        if (ok) return addr;
+    }
+}
+
+// Deallocation (Sec. 5): clear the unit's bit in its memory block's bitmap.
+__device__ __forceinline__ void deallocate(const TableView& T, uint32_t addr) {
+    uint32_t block = addr >> 10, word = (addr >> 5) & 31u, bit = addr & 31u;
+    atomicAnd(T.bitmaps + (uint64_t)block * 32 + word, ~(1u << bit));
+}
+
+}  // namespace slab

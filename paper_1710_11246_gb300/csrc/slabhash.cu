@@ -1,0 +1,505 @@
+// Host side of the slab-hash C ABI (include/slabhash.h) and the table's
+// maintenance kernels: fill, chain statistics, export, hash, and the SlabAlloc
+// allocation / deallocation batches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <new>
+
+#include "../../include/slabhash.h"
+#include "slab_device.cuh"
+#include "slab_wcws.cuh"
+
+using namespace slab;
+
+struct slab_table {
+    int device = 0;
+    int sm_count = 0;
+    uint32_t num_buckets = 0;
+    int mode = 0;
+    uint32_t hash_a = 0, hash_b = 0;
+    uint64_t fastmod_m = 0;
+    uint64_t pool_slabs = 0;
+    uint32_t num_blocks = 0;
+    uint32_t* d_slabs = nullptr;      // base slabs then pool
+    uint32_t* d_bitmaps = nullptr;
+    uint32_t* d_misc = nullptr;       // [0] status word, [2..] 8 x u64 counters
+    uint64_t device_bytes = 0;
+    int max_smem_optin = 0;
+    slab_config cfg{};
+    uint32_t epoch = 0;
+};
+
+namespace {
+
+constexpr uint32_t kDefaultIterLimit = 1u << 22;
+constexpr uint32_t kDefaultRandomProbes = 256;
+
+unsigned long long* counters(const slab_table* t) {
+    return reinterpret_cast<unsigned long long*>(t->d_misc + 2);
+}
+
+TableView view(slab_table* t) {
+    TableView v;
+    v.slabs = t->d_slabs;
+    v.pool = t->d_slabs + (uint64_t)t->num_buckets * kWordsPerSlab;
+    v.bitmaps = t->d_bitmaps;
+    v.status = t->d_misc;
+    v.fastmod_m = t->fastmod_m;
+    v.num_buckets = t->num_buckets;
+    v.hash_a = t->hash_a;
+    v.hash_b = t->hash_b;
+    v.num_blocks = t->num_blocks;
+    v.pool_units = (uint32_t)t->pool_slabs;
+    v.iter_limit = t->cfg.iter_limit;
+    v.random_probes = t->cfg.random_probes;
+    v.epoch = ++t->epoch;
+    return v;
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int launch_rc() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SLAB_OK : SLAB_ERR_CUDA;
+}
+
+bool valid_config(const slab_config& c) {
+    return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
+           c.threads_per_block >= 32 && c.threads_per_block <= 1024 && c.threads_per_block % 32 == 0 &&
+           c.blocks_per_sm >= 0 && c.blocks_per_sm <= 64 && c.iter_limit >= 1 && c.random_probes <= (1u << 20) &&
+           // staged kernels hold 4 KB of shared memory per warp
+           (c.variant != SLAB_VARIANT_STAGED || c.threads_per_block / 32 * 4096 <= 227 * 1024);
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void fill_kernel(uint4* slabs, uint64_t n16, uint4* bitmaps, uint64_t b16, uint32_t* misc) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4 ones = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (uint64_t i = tid; i < n16; i += stride) slabs[i] = ones;
+    for (uint64_t i = tid; i < b16; i += stride) bitmaps[i] = zero;
+    if (tid == 0) misc[0] = 0;
+}
+
+// One warp per bucket: walk the list, count used and live key lanes and slabs,
+// and check that used slots form a prefix in (slab, lane) order.
+template <bool kKeyOnly>
+__global__ void stats_kernel(TableView T, uint32_t* slots, uint32_t* slabs, unsigned long long* acc) {
+    constexpr uint32_t kMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    constexpr uint32_t kPerSlab = kKeyOnly ? 30u : 15u;
+    const uint32_t lane = lane_id();
+    const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long live_sum = 0, used_sum = 0, slab_sum = 0, bad = 0, linked = 0;
+    for (uint32_t b = warp_gid; b < T.num_buckets; b += nwarps) {
+        uint32_t cur = kEmptyKey, used = 0, live = 0, n = 0;
+        bool prefix_ok = true, prev_full = true;
+        // a list can hold at most every pool slab plus its base slab
+        for (uint64_t guard = 0; guard <= (uint64_t)T.num_blocks * kUnitsPerBlock; ++guard) {
+            const uint32_t w = ld_coherent(slab_ptr(T, b, cur) + lane);
+            const uint32_t u = __ballot_sync(kFull, w != kEmptyKey) & kMask;
+            const uint32_t l = __ballot_sync(kFull, w != kEmptyKey && w != kTombstone) & kMask;
+            const uint32_t cnt = __popc(u);
+            // used lanes must be the lowest `cnt` key lanes, and only the last slab may be partial
+            uint32_t want = 0, m = kMask;
+            for (uint32_t i = 0; i < cnt; ++i) { want |= m & (0u - m); m &= m - 1u; }
+            if (u != want || !prev_full) prefix_ok = false;
+            prev_full = cnt == kPerSlab;
+            used += cnt;
+            live += __popc(l);
+            ++n;
+            const uint32_t nx = __shfl_sync(kFull, w, kAddressLane);
+            if (nx == kEmptyKey) break;
+            if (!valid_next(T, nx)) {
+                prefix_ok = false;
+                break;
+            }
+            cur = nx;
+        }
+        if (lane == 0) {
+            if (slots) slots[b] = used;
+            if (slabs) slabs[b] = n;
+        }
+        live_sum += live; used_sum += used; slab_sum += n; linked += n - 1; bad += prefix_ok ? 0 : 1;
+    }
+    if (lane == 0) {
+        atomicAdd(acc + 0, live_sum);
+        atomicAdd(acc + 1, used_sum);
+        atomicAdd(acc + 2, slab_sum);
+        atomicAdd(acc + 4, bad);
+        atomicAdd(acc + 5, linked);
+    }
+}
+
+__global__ void popcount_kernel(const uint32_t* words, uint64_t n, unsigned long long* acc) {
+    unsigned long long c = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        c += __popc(words[i]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(acc + 3, c);
+}
+
+template <bool kKeyOnly>
+__global__ void export_kernel(TableView T, uint32_t* ob, uint32_t* ok, uint32_t* ov, uint64_t cap,
+                              unsigned long long* count) {
+    constexpr uint32_t kMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    const uint32_t lane = lane_id();
+    const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t b = warp_gid; b < T.num_buckets; b += nwarps) {
+        uint32_t cur = kEmptyKey;
+        for (uint64_t guard = 0; guard <= (uint64_t)T.num_blocks * kUnitsPerBlock; ++guard) {
+            const uint32_t w = ld_coherent(slab_ptr(T, b, cur) + lane);
+            const uint32_t v = __shfl_down_sync(kFull, w, 1);
+            const uint32_t l = __ballot_sync(kFull, w != kEmptyKey && w != kTombstone) & kMask;
+            unsigned long long base = 0;
+            if (lane == 0 && l) base = atomicAdd(count, (unsigned long long)__popc(l));
+            base = __shfl_sync(kFull, base, 0);
+            if ((l >> lane) & 1u) {
+                const uint64_t at = base + __popc(l & ((1u << lane) - 1u));
+                if (at < cap) {
+                    ok[at] = w;
+                    if (ob) ob[at] = b;
+                    if (ov) ov[at] = kKeyOnly ? 0u : v;
+                }
+            }
+            const uint32_t nx = __shfl_sync(kFull, w, kAddressLane);
+            if (nx == kEmptyKey || !valid_next(T, nx)) break;
+            cur = nx;
+        }
+    }
+}
+
+__global__ void bucket_kernel(TableView T, const uint32_t* keys, uint32_t* out, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = bucket_of(T, keys[i]);
+}
+
+// SlabAlloc microbenchmark: one request per lane, served one at a time per warp.
+__global__ void alloc_kernel(TableView T, uint32_t* out, uint32_t n) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    AllocCtx ac{kNoBlock, 0u, 0u};
+    bool failed = false;
+    for (uint32_t tile = warp_gid; tile < (n + 31u) / 32u; tile += nwarps) {
+        const uint32_t idx = tile * 32u + lane;
+        uint32_t queue = __ballot_sync(kFull, idx < n);
+        uint32_t mine = kEmptyKey;
+        while (queue) {
+            const int s = __ffs(queue) - 1;
+            queue &= queue - 1u;
+            const uint32_t a = failed ? kAllocFailed : warp_allocate(T, ac, warp_gid);
+            if (a == kAllocFailed) failed = true;
+            if ((int)lane == s) mine = a;
+        }
+        if (idx < n) out[idx] = mine;
+    }
+    if (failed && lane == 0) set_flag(T, kFlagOutOfSlabs);
+}
+
+__global__ void free_kernel(TableView T, const uint32_t* addrs, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t a = addrs[i];
+        if (a != kEmptyKey && (a >> 10) < T.num_blocks) deallocate(T, a);
+    }
+}
+
+// ------------------------------------------------------------ batch launch
+template <int kKind, bool kKeyOnly>
+int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
+    if (a.n == 0) return SLAB_OK;
+    const TableView T = view(t);
+    const int tpb = t->cfg.threads_per_block;
+    const int wpb = tpb / 32;
+    if (t->cfg.variant == SLAB_VARIANT_DIRECT) {
+        auto k = direct_kernel<kKind, kKeyOnly>;
+        int bps = t->cfg.blocks_per_sm;
+        if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, tpb, 0) != cudaSuccess)
+            return SLAB_ERR_CUDA;
+        const uint64_t tiles = (a.n + 31u) / 32u;
+        const uint64_t want = (tiles + wpb - 1) / wpb;
+        const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
+        k<<<grid, tpb, 0, S(stream)>>>(T, a);
+    } else {
+        auto k = staged_kernel<kKind, kKeyOnly>;
+        const size_t smem = (size_t)wpb * kStageWordsPerWarp * 4;
+        if ((int)smem > t->max_smem_optin) return SLAB_ERR_INVALID_ARG;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return SLAB_ERR_CUDA;
+        int bps = t->cfg.blocks_per_sm;
+        if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, tpb, smem) != cudaSuccess)
+            return SLAB_ERR_CUDA;
+        const uint64_t warps_wanted = (a.n + 31u) / 32u;
+        const uint64_t want = (warps_wanted + wpb - 1) / wpb;
+        const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
+        const uint64_t warps = grid * wpb;
+        const uint32_t per_warp = (uint32_t)((a.n + warps - 1) / warps);
+        k<<<(uint32_t)grid, tpb, smem, S(stream)>>>(T, a, per_warp);
+    }
+    return launch_rc();
+}
+
+template <int kKind>
+int dispatch(slab_table* t, const BatchArgs& a, void* stream) {
+    return t->mode == SLAB_MODE_KEY_ONLY ? launch_batch<kKind, true>(t, a, stream)
+                                         : launch_batch<kKind, false>(t, a, stream);
+}
+
+uint32_t util_grid(const slab_table* t, uint64_t work, int tpb) {
+    const uint64_t want = (work + tpb - 1) / tpb;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)t->sm_count * 8));
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* slab_error_string(int rc) {
+    switch (rc) {
+        case SLAB_OK: return "ok";
+        case SLAB_ERR_INVALID_ARG: return "invalid argument";
+        case SLAB_ERR_RESERVED_KEY: return "a batch held a reserved (sentinel) key";
+        case SLAB_ERR_OUT_OF_SLABS: return "SlabAlloc pool exhausted";
+        case SLAB_ERR_ITER_LIMIT: return "an op reached the iteration cap";
+        case SLAB_ERR_CUDA: return "CUDA error";
+        case SLAB_ERR_CORRUPT: return "a slab list held a next pointer outside the pool";
+        default: return "unknown error";
+    }
+}
+
+int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b,
+                uint64_t pool_slabs, slab_table** out) {
+    if (!out) return SLAB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (num_buckets == 0 || (mode != SLAB_MODE_KEY_VALUE && mode != SLAB_MODE_KEY_ONLY) ||
+        hash_a == 0 || hash_a >= kPrime || hash_b >= kPrime || pool_slabs == 0)
+        return SLAB_ERR_INVALID_ARG;
+    const uint64_t blocks = (pool_slabs + kUnitsPerBlock - 1) / kUnitsPerBlock;
+    const uint64_t pool = blocks * kUnitsPerBlock;
+    // every pool address must differ from the empty pointer, and the base slabs
+    // plus the pool must be indexable by 32 bits
+    if (blocks >= (1ull << 22) || (uint64_t)num_buckets + pool > 0xFFFFFFFEull) return SLAB_ERR_INVALID_ARG;
+
+    slab_table* t = new (std::nothrow) slab_table();
+    if (!t) return SLAB_ERR_CUDA;
+    if (cudaGetDevice(&t->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&t->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device) !=
+            cudaSuccess) {
+        delete t;
+        return SLAB_ERR_CUDA;
+    }
+    t->num_buckets = num_buckets;
+    t->mode = mode;
+    t->hash_a = hash_a;
+    t->hash_b = hash_b;
+    t->fastmod_m = UINT64_MAX / num_buckets + 1;  // wraps to 0 for B = 1, which yields 0 as needed
+    t->pool_slabs = pool;
+    t->num_blocks = (uint32_t)blocks;
+    const uint64_t slab_bytes = ((uint64_t)num_buckets + pool) * 128ull;
+    const uint64_t bitmap_bytes = blocks * 128ull;
+    if (cudaMalloc(&t->d_slabs, slab_bytes) != cudaSuccess) { delete t; cudaGetLastError(); return SLAB_ERR_CUDA; }
+    if (cudaMalloc(&t->d_bitmaps, bitmap_bytes) != cudaSuccess ||
+        cudaMalloc(&t->d_misc, 128) != cudaSuccess) {
+        cudaFree(t->d_slabs);
+        cudaFree(t->d_bitmaps);
+        delete t;
+        cudaGetLastError();
+        return SLAB_ERR_CUDA;
+    }
+    t->device_bytes = slab_bytes + bitmap_bytes + 128;
+    t->cfg.variant = SLAB_VARIANT_STAGED;
+    t->cfg.threads_per_block = 256;
+    t->cfg.blocks_per_sm = 0;
+    t->cfg.iter_limit = kDefaultIterLimit;
+    t->cfg.random_probes = kDefaultRandomProbes;
+    if (cudaMemset(t->d_misc, 0, 128) != cudaSuccess || slab_reset(t, nullptr) != SLAB_OK ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        slab_destroy(t);
+        return SLAB_ERR_CUDA;
+    }
+    *out = t;
+    return SLAB_OK;
+}
+
+void slab_destroy(slab_table* t) {
+    if (!t) return;
+    cudaDeviceSynchronize();
+    cudaFree(t->d_slabs);
+    cudaFree(t->d_bitmaps);
+    cudaFree(t->d_misc);
+    delete t;
+}
+
+int slab_reset(slab_table* t, void* stream) {
+    if (!t) return SLAB_ERR_INVALID_ARG;
+    const uint64_t n16 = ((uint64_t)t->num_buckets + t->pool_slabs) * 8;  // uint4 per 16 bytes
+    const uint64_t b16 = (uint64_t)t->num_blocks * 8;
+    fill_kernel<<<util_grid(t, n16, 256), 256, 0, S(stream)>>>(
+        reinterpret_cast<uint4*>(t->d_slabs), n16, reinterpret_cast<uint4*>(t->d_bitmaps), b16, t->d_misc);
+    return launch_rc();
+}
+
+int slab_get_info(const slab_table* t, slab_info* out) {
+    if (!t || !out) return SLAB_ERR_INVALID_ARG;
+    out->num_buckets = t->num_buckets;
+    out->mode = t->mode;
+    out->elements_per_slab = t->mode == SLAB_MODE_KEY_ONLY ? 30u : 15u;
+    out->hash_a = t->hash_a;
+    out->hash_b = t->hash_b;
+    out->pool_slabs = t->pool_slabs;
+    out->num_memory_blocks = t->num_blocks;
+    out->blocks_per_super = kBlocksPerSuper;
+    out->num_super_blocks = (t->num_blocks + kBlocksPerSuper - 1) / kBlocksPerSuper;
+    out->sm_count = (uint32_t)t->sm_count;
+    out->device_bytes = t->device_bytes;
+    return SLAB_OK;
+}
+
+int slab_get_config(const slab_table* t, slab_config* out) {
+    if (!t || !out) return SLAB_ERR_INVALID_ARG;
+    *out = t->cfg;
+    return SLAB_OK;
+}
+
+int slab_set_config(slab_table* t, const slab_config* cfg) {
+    if (!t || !cfg || !valid_config(*cfg)) return SLAB_ERR_INVALID_ARG;
+    t->cfg = *cfg;
+    return SLAB_OK;
+}
+
+int slab_insert_batch(slab_table* t, const uint32_t* d_keys, const uint32_t* d_values, uint8_t* d_found,
+                      uint32_t n, void* stream) {
+    if (!t || (n && !d_keys) || (n && !d_values && t->mode == SLAB_MODE_KEY_VALUE)) return SLAB_ERR_INVALID_ARG;
+    BatchArgs a{nullptr, d_keys, d_values, nullptr, d_found, n};
+    return dispatch<kKindInsert>(t, a, stream);
+}
+
+int slab_delete_batch(slab_table* t, const uint32_t* d_keys, uint8_t* d_found, uint32_t n, void* stream) {
+    if (!t || (n && !d_keys)) return SLAB_ERR_INVALID_ARG;
+    BatchArgs a{nullptr, d_keys, nullptr, nullptr, d_found, n};
+    return dispatch<kKindDelete>(t, a, stream);
+}
+
+int slab_search_batch(slab_table* t, const uint32_t* d_keys, uint32_t* d_values_out, uint8_t* d_found,
+                      uint32_t n, void* stream) {
+    if (!t || (n && (!d_keys || !d_values_out))) return SLAB_ERR_INVALID_ARG;
+    BatchArgs a{nullptr, d_keys, nullptr, d_values_out, d_found, n};
+    return dispatch<kKindSearch>(t, a, stream);
+}
+
+int slab_mixed_batch(slab_table* t, const uint8_t* d_ops, const uint32_t* d_keys, const uint32_t* d_values,
+                     uint32_t* d_results, uint8_t* d_found, uint32_t n, void* stream) {
+    if (!t || (n && (!d_ops || !d_keys || !d_results)) ||
+        (n && !d_values && t->mode == SLAB_MODE_KEY_VALUE))
+        return SLAB_ERR_INVALID_ARG;
+    BatchArgs a{d_ops, d_keys, d_values, d_results, d_found, n};
+    return dispatch<kKindMixed>(t, a, stream);
+}
+
+int slab_status(slab_table* t, void* stream, uint32_t* h_flags) {
+    if (!t) return SLAB_ERR_INVALID_ARG;
+    uint32_t f = 0;
+    if (cudaMemcpyAsync(&f, t->d_misc, 4, cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess ||
+        cudaMemsetAsync(t->d_misc, 0, 4, S(stream)) != cudaSuccess ||
+        cudaStreamSynchronize(S(stream)) != cudaSuccess)
+        return SLAB_ERR_CUDA;
+    if (h_flags) *h_flags = f;
+    if (f & kFlagBadPointer) return SLAB_ERR_CORRUPT;
+    if (f & kFlagOutOfSlabs) return SLAB_ERR_OUT_OF_SLABS;
+    if (f & kFlagIterLimit) return SLAB_ERR_ITER_LIMIT;
+    if (f & kFlagReserved) return SLAB_ERR_RESERVED_KEY;
+    return SLAB_OK;
+}
+
+int slab_stats(slab_table* t, uint32_t* d_slots, uint32_t* d_slabs, uint64_t* h_totals, void* stream) {
+    if (!t) return SLAB_ERR_INVALID_ARG;
+    unsigned long long* acc = counters(t);
+    if (cudaMemsetAsync(acc, 0, 8 * sizeof(unsigned long long), S(stream)) != cudaSuccess) return SLAB_ERR_CUDA;
+    const TableView T = view(t);
+    const uint32_t grid = util_grid(t, (uint64_t)t->num_buckets * 32, 256);
+    if (t->mode == SLAB_MODE_KEY_ONLY)
+        stats_kernel<true><<<grid, 256, 0, S(stream)>>>(T, d_slots, d_slabs, acc);
+    else
+        stats_kernel<false><<<grid, 256, 0, S(stream)>>>(T, d_slots, d_slabs, acc);
+    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    const uint64_t words = (uint64_t)t->num_blocks * 32;
+    popcount_kernel<<<util_grid(t, words, 256), 256, 0, S(stream)>>>(t->d_bitmaps, words, acc);
+    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    if (h_totals) {
+        unsigned long long h[8];
+        if (cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess ||
+            cudaStreamSynchronize(S(stream)) != cudaSuccess)
+            return SLAB_ERR_CUDA;
+        for (int i = 0; i < 6; ++i) h_totals[i] = h[i];
+    }
+    return SLAB_OK;
+}
+
+int slab_export(slab_table* t, uint32_t* d_buckets, uint32_t* d_keys, uint32_t* d_values, uint64_t capacity,
+                uint64_t* h_count, void* stream) {
+    if (!t || !h_count || (capacity && !d_keys)) return SLAB_ERR_INVALID_ARG;
+    unsigned long long* acc = counters(t);
+    if (cudaMemsetAsync(acc + 6, 0, sizeof(unsigned long long), S(stream)) != cudaSuccess) return SLAB_ERR_CUDA;
+    const TableView T = view(t);
+    const uint32_t grid = util_grid(t, (uint64_t)t->num_buckets * 32, 256);
+    if (t->mode == SLAB_MODE_KEY_ONLY)
+        export_kernel<true><<<grid, 256, 0, S(stream)>>>(T, d_buckets, d_keys, d_values, capacity, acc + 6);
+    else
+        export_kernel<false><<<grid, 256, 0, S(stream)>>>(T, d_buckets, d_keys, d_values, capacity, acc + 6);
+    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    unsigned long long c = 0;
+    if (cudaMemcpyAsync(&c, acc + 6, sizeof(c), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess ||
+        cudaStreamSynchronize(S(stream)) != cudaSuccess)
+        return SLAB_ERR_CUDA;
+    *h_count = c;
+    return SLAB_OK;
+}
+
+int slab_bucket_of(slab_table* t, const uint32_t* d_keys, uint32_t* d_buckets_out, uint32_t n, void* stream) {
+    if (!t || (n && (!d_keys || !d_buckets_out))) return SLAB_ERR_INVALID_ARG;
+    if (n == 0) return SLAB_OK;
+    const TableView T = view(t);
+    bucket_kernel<<<util_grid(t, n, 256), 256, 0, S(stream)>>>(T, d_keys, d_buckets_out, n);
+    return launch_rc();
+}
+
+int slab_alloc_batch(slab_table* t, uint32_t* d_addrs_out, uint32_t n, void* stream) {
+    if (!t || (n && !d_addrs_out)) return SLAB_ERR_INVALID_ARG;
+    if (n == 0) return SLAB_OK;
+    const TableView T = view(t);
+    const int tpb = t->cfg.threads_per_block;
+    int bps = t->cfg.blocks_per_sm;
+    if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, alloc_kernel, tpb, 0) != cudaSuccess)
+        return SLAB_ERR_CUDA;
+    const uint64_t warps = (n + 31u) / 32u;
+    const uint64_t want = (warps * 32 + tpb - 1) / tpb;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
+    alloc_kernel<<<grid, tpb, 0, S(stream)>>>(T, d_addrs_out, n);
+    return launch_rc();
+}
+
+int slab_free_batch(slab_table* t, const uint32_t* d_addrs, uint32_t n, void* stream) {
+    if (!t || (n && !d_addrs)) return SLAB_ERR_INVALID_ARG;
+    if (n == 0) return SLAB_OK;
+    const TableView T = view(t);
+    free_kernel<<<util_grid(t, n, 256), 256, 0, S(stream)>>>(T, d_addrs, n);
+    return launch_rc();
+}
+
+int slab_copy_bitmaps(const slab_table* t, uint32_t* d_dst, uint64_t n_words, void* stream) {
+    if (!t || !d_dst || n_words != (uint64_t)t->num_blocks * 32) return SLAB_ERR_INVALID_ARG;
+    return cudaMemcpyAsync(d_dst, t->d_bitmaps, n_words * 4, cudaMemcpyDeviceToDevice, S(stream)) == cudaSuccess
+               ? SLAB_OK
+               : SLAB_ERR_CUDA;
+}
+
+}  // extern "C"

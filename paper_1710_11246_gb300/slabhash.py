@@ -1,0 +1,357 @@
+"""Python binding of libslabhash.so (include/slabhash.h): argument marshalling only.
+
+Every function keeps the C name and forwards device pointers of torch CUDA
+tensors plus the torch stream handle; all work runs in the library's kernels.
+There is no CPU path: if the library cannot be loaded, the import of the
+binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+SLAB_MODE_KEY_VALUE, SLAB_MODE_KEY_ONLY = 0, 1
+SLAB_OP_INSERT, SLAB_OP_DELETE, SLAB_OP_SEARCH = 0, 1, 2
+SLAB_OK, SLAB_ERR_INVALID_ARG, SLAB_ERR_RESERVED_KEY = 0, 1, 2
+SLAB_ERR_OUT_OF_SLABS, SLAB_ERR_ITER_LIMIT, SLAB_ERR_CUDA, SLAB_ERR_CORRUPT = 3, 4, 5, 6
+SLAB_FLAG_RESERVED_KEY, SLAB_FLAG_OUT_OF_SLABS, SLAB_FLAG_ITER_LIMIT, SLAB_FLAG_BAD_POINTER = 1, 2, 4, 8
+SLAB_EMPTY_KEY = SLAB_NOT_FOUND = 0xFFFFFFFF
+SLAB_TOMBSTONE_KEY = 0xFFFFFFFE
+SLAB_HASH_PRIME = 4294967291
+SLAB_VARIANT_STAGED, SLAB_VARIANT_DIRECT = 0, 1
+
+EXPORTED = [
+    "slab_create", "slab_destroy", "slab_reset", "slab_get_info", "slab_get_config", "slab_set_config",
+    "slab_insert_batch", "slab_delete_batch", "slab_search_batch", "slab_mixed_batch", "slab_status",
+    "slab_stats", "slab_export", "slab_bucket_of", "slab_alloc_batch", "slab_free_batch",
+    "slab_copy_bitmaps", "slab_error_string", "slab_probe_random_lines", "slab_probe_random_cas",
+]
+
+
+class SlabConfig(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("iter_limit", C.c_uint32), ("random_probes", C.c_uint32)]
+
+
+class SlabInfo(C.Structure):
+    _fields_ = [("num_buckets", C.c_uint32), ("mode", C.c_int32), ("elements_per_slab", C.c_uint32),
+                ("hash_a", C.c_uint32), ("hash_b", C.c_uint32), ("pool_slabs", C.c_uint64),
+                ("num_memory_blocks", C.c_uint32), ("blocks_per_super", C.c_uint32),
+                ("num_super_blocks", C.c_uint32), ("sm_count", C.c_uint32), ("device_bytes", C.c_uint64)]
+
+
+class SlabError(RuntimeError):
+    def __init__(self, rc: int, what: str = ""):
+        self.rc = rc
+        super().__init__(f"{what}: {slab_error_string(rc)} (rc={rc})" if what else slab_error_string(rc))
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(build_if_stale: bool = True) -> C.CDLL:
+    """Load the in-tree libslabhash.so, building it from source when it is stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_stale and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing; build it with paper_1710_11246_gb300.build.build()")
+        lib = C.CDLL(_build.LIB)
+        vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+        sig = {
+            "slab_create": (i32, [u32, i32, u32, u32, u64, C.POINTER(vp)]),
+            "slab_destroy": (None, [vp]),
+            "slab_reset": (i32, [vp, vp]),
+            "slab_get_info": (i32, [vp, C.POINTER(SlabInfo)]),
+            "slab_get_config": (i32, [vp, C.POINTER(SlabConfig)]),
+            "slab_set_config": (i32, [vp, C.POINTER(SlabConfig)]),
+            "slab_insert_batch": (i32, [vp, vp, vp, vp, u32, vp]),
+            "slab_delete_batch": (i32, [vp, vp, vp, u32, vp]),
+            "slab_search_batch": (i32, [vp, vp, vp, vp, u32, vp]),
+            "slab_mixed_batch": (i32, [vp, vp, vp, vp, vp, vp, u32, vp]),
+            "slab_status": (i32, [vp, vp, C.POINTER(u32)]),
+            "slab_stats": (i32, [vp, vp, vp, C.POINTER(u64), vp]),
+            "slab_export": (i32, [vp, vp, vp, vp, u64, C.POINTER(u64), vp]),
+            "slab_bucket_of": (i32, [vp, vp, vp, u32, vp]),
+            "slab_alloc_batch": (i32, [vp, vp, u32, vp]),
+            "slab_free_batch": (i32, [vp, vp, u32, vp]),
+            "slab_copy_bitmaps": (i32, [vp, vp, u64, vp]),
+            "slab_error_string": (C.c_char_p, [i32]),
+            "slab_probe_random_lines": (i32, [vp, u64, u64, u32, i32, i32, vp, vp]),
+            "slab_probe_random_cas": (i32, [vp, u64, u64, u32, i32, i32, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def slab_error_string(rc: int) -> str:
+    return load_library().slab_error_string(int(rc)).decode()
+
+
+# ------------------------------------------------------------------ marshalling
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dptr(t, itemsize: int, n: int, name: str, nullable: bool = False):
+    if t is None:
+        if nullable:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous() or t.element_size() != itemsize:
+        raise ValueError(f"{name} must be contiguous with {itemsize}-byte elements")
+    if t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {n}")
+    return t.data_ptr() if n or t.numel() else None
+
+
+def _check(rc: int, what: str):
+    if rc != SLAB_OK:
+        raise SlabError(rc, what)
+
+
+# ------------------------------------------------------------------ C-name API
+def slab_create(num_buckets: int, mode: int, hash_a: int, hash_b: int, pool_slabs: int) -> int:
+    h = C.c_void_p()
+    _check(load_library().slab_create(num_buckets, mode, hash_a, hash_b, pool_slabs, C.byref(h)),
+           "slab_create")
+    return h.value
+
+
+def slab_destroy(t: int) -> None:
+    load_library().slab_destroy(t)
+
+
+def slab_reset(t: int, stream=None) -> None:
+    _check(load_library().slab_reset(t, _stream(stream)), "slab_reset")
+
+
+def slab_get_info(t: int) -> SlabInfo:
+    info = SlabInfo()
+    _check(load_library().slab_get_info(t, C.byref(info)), "slab_get_info")
+    return info
+
+
+def slab_get_config(t: int) -> SlabConfig:
+    cfg = SlabConfig()
+    _check(load_library().slab_get_config(t, C.byref(cfg)), "slab_get_config")
+    return cfg
+
+
+def slab_set_config(t: int, cfg: SlabConfig) -> None:
+    _check(load_library().slab_set_config(t, C.byref(cfg)), "slab_set_config")
+
+
+def slab_insert_batch(t: int, keys, values, found=None, n: int | None = None, stream=None) -> None:
+    n = keys.numel() if n is None else n
+    _check(load_library().slab_insert_batch(
+        t, _dptr(keys, 4, n, "keys"), _dptr(values, 4, n, "values", nullable=True),
+        _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)), "slab_insert_batch")
+
+
+def slab_delete_batch(t: int, keys, found=None, n: int | None = None, stream=None) -> None:
+    n = keys.numel() if n is None else n
+    _check(load_library().slab_delete_batch(
+        t, _dptr(keys, 4, n, "keys"), _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)),
+        "slab_delete_batch")
+
+
+def slab_search_batch(t: int, keys, values_out, found=None, n: int | None = None, stream=None) -> None:
+    n = keys.numel() if n is None else n
+    _check(load_library().slab_search_batch(
+        t, _dptr(keys, 4, n, "keys"), _dptr(values_out, 4, n, "values_out"),
+        _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)), "slab_search_batch")
+
+
+def slab_mixed_batch(t: int, ops, keys, values, results, found=None, n: int | None = None,
+                     stream=None) -> None:
+    n = keys.numel() if n is None else n
+    _check(load_library().slab_mixed_batch(
+        t, _dptr(ops, 1, n, "ops"), _dptr(keys, 4, n, "keys"), _dptr(values, 4, n, "values", nullable=True),
+        _dptr(results, 4, n, "results"), _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)),
+        "slab_mixed_batch")
+
+
+def slab_status(t: int, stream=None) -> tuple[int, int]:
+    """(return code, status flags); synchronizes the stream and clears the flags."""
+    flags = C.c_uint32(0)
+    rc = load_library().slab_status(t, _stream(stream), C.byref(flags))
+    if rc == SLAB_ERR_CUDA or rc == SLAB_ERR_INVALID_ARG:
+        raise SlabError(rc, "slab_status")
+    return rc, flags.value
+
+
+def slab_stats(t: int, slots=None, slabs=None, stream=None) -> dict:
+    info = slab_get_info(t)
+    tot = (C.c_uint64 * 6)()
+    _check(load_library().slab_stats(
+        t, _dptr(slots, 4, info.num_buckets, "slots", nullable=True),
+        _dptr(slabs, 4, info.num_buckets, "slabs", nullable=True), tot, _stream(stream)), "slab_stats")
+    return dict(live=tot[0], slots=tot[1], slabs=tot[2], pool_allocated=tot[3], prefix_violations=tot[4],
+                linked=tot[5])
+
+
+def slab_export(t: int, buckets, keys, values, capacity: int, stream=None) -> int:
+    count = C.c_uint64(0)
+    _check(load_library().slab_export(
+        t, _dptr(buckets, 4, capacity, "buckets", nullable=True), _dptr(keys, 4, capacity, "keys", nullable=True),
+        _dptr(values, 4, capacity, "values", nullable=True), capacity, C.byref(count), _stream(stream)),
+        "slab_export")
+    return count.value
+
+
+def slab_bucket_of(t: int, keys, buckets_out, n: int | None = None, stream=None) -> None:
+    n = keys.numel() if n is None else n
+    _check(load_library().slab_bucket_of(t, _dptr(keys, 4, n, "keys"), _dptr(buckets_out, 4, n, "buckets_out"),
+                                         n, _stream(stream)), "slab_bucket_of")
+
+
+def slab_alloc_batch(t: int, addrs_out, n: int | None = None, stream=None) -> None:
+    n = addrs_out.numel() if n is None else n
+    _check(load_library().slab_alloc_batch(t, _dptr(addrs_out, 4, n, "addrs_out"), n, _stream(stream)),
+           "slab_alloc_batch")
+
+
+def slab_free_batch(t: int, addrs, n: int | None = None, stream=None) -> None:
+    n = addrs.numel() if n is None else n
+    _check(load_library().slab_free_batch(t, _dptr(addrs, 4, n, "addrs"), n, _stream(stream)),
+           "slab_free_batch")
+
+
+def slab_copy_bitmaps(t: int, dst, stream=None) -> None:
+    info = slab_get_info(t)
+    n = info.num_memory_blocks * 32
+    _check(load_library().slab_copy_bitmaps(t, _dptr(dst, 4, n, "dst"), n, _stream(stream)),
+           "slab_copy_bitmaps")
+
+
+def slab_probe_random_lines(buf, footprint_lines: int, n_reads: int, seed: int, lines_in_flight: int,
+                            threads_per_block: int, sink, stream=None) -> None:
+    _check(load_library().slab_probe_random_lines(
+        _dptr(buf, 4, footprint_lines * 32, "buf"), footprint_lines, n_reads, seed, lines_in_flight,
+        threads_per_block, _dptr(sink, 4, 1, "sink"), _stream(stream)), "slab_probe_random_lines")
+
+
+def slab_probe_random_cas(buf, footprint_lines: int, n_ops: int, seed: int, ops_in_flight: int,
+                          threads_per_block: int, stream=None) -> None:
+    _check(load_library().slab_probe_random_cas(
+        _dptr(buf, 8, footprint_lines * 16, "buf"), footprint_lines, n_ops, seed, ops_in_flight,
+        threads_per_block, _stream(stream)), "slab_probe_random_cas")
+
+
+# ------------------------------------------------------------------ convenience
+def as_device_u32(a, device="cuda") -> torch.Tensor:
+    """A uint32 numpy array (or tensor) as a contiguous int32-typed CUDA tensor of the same bits."""
+    import numpy as np
+    if isinstance(a, torch.Tensor):
+        return a.contiguous().to(device)
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)).to(device)
+
+
+def to_host_u32(t: torch.Tensor):
+    import numpy as np
+    return t.cpu().numpy().view(np.uint32)
+
+
+class SlabHash:
+    """Owns one table; methods take and return torch CUDA tensors (int32 storage of uint32 bits)."""
+
+    def __init__(self, num_buckets: int, hash_a: int, hash_b: int, pool_slabs: int,
+                 mode: int = SLAB_MODE_KEY_VALUE):
+        self.handle = slab_create(num_buckets, mode, hash_a, hash_b, pool_slabs)
+        self.info = slab_get_info(self.handle)
+        self.mode = mode
+
+    def close(self):
+        if getattr(self, "handle", None):
+            slab_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, **kw):
+        cfg = slab_get_config(self.handle)
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        slab_set_config(self.handle, cfg)
+
+    def config(self) -> dict:
+        cfg = slab_get_config(self.handle)
+        return {f: getattr(cfg, f) for f, _ in cfg._fields_}
+
+    def reset(self, stream=None):
+        slab_reset(self.handle, stream)
+
+    def insert(self, keys, values=None, found=None, stream=None):
+        slab_insert_batch(self.handle, keys, values, found, stream=stream)
+
+    def delete(self, keys, found=None, stream=None):
+        slab_delete_batch(self.handle, keys, found, stream=stream)
+
+    def search(self, keys, values_out=None, found=None, stream=None):
+        if values_out is None:
+            values_out = torch.empty_like(keys)
+        slab_search_batch(self.handle, keys, values_out, found, stream=stream)
+        return values_out
+
+    def mixed(self, ops, keys, values, results=None, found=None, stream=None):
+        if results is None:
+            results = torch.empty_like(keys)
+        slab_mixed_batch(self.handle, ops, keys, values, results, found, stream=stream)
+        return results
+
+    def status(self, stream=None):
+        return slab_status(self.handle, stream)
+
+    def stats(self, per_bucket: bool = False, stream=None):
+        if not per_bucket:
+            return slab_stats(self.handle, stream=stream)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        slots = torch.empty(self.info.num_buckets, dtype=torch.int32, device=dev)
+        slabs = torch.empty_like(slots)
+        tot = slab_stats(self.handle, slots, slabs, stream=stream)
+        return slots, slabs, tot
+
+    def export(self, stream=None):
+        n = slab_export(self.handle, None, None, None, 0, stream=stream)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        b = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        k = torch.empty_like(b)
+        v = torch.empty_like(b)
+        m = slab_export(self.handle, b, k, v, n, stream=stream)
+        assert m == n
+        return b[:n], k[:n], v[:n]
+
+    def bitmaps(self, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = torch.empty(self.info.num_memory_blocks * 32, dtype=torch.int32, device=dev)
+        slab_copy_bitmaps(self.handle, out, stream=stream)
+        return out
+
+    def buckets_of(self, keys, stream=None):
+        out = torch.empty_like(keys)
+        slab_bucket_of(self.handle, keys, out, stream=stream)
+        return out

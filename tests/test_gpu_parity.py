@@ -1,0 +1,264 @@
+"""GPU slab hash vs the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hash_of
+from paper_1710_11246_gb300 import slabhash as sh
+from paper_1710_11246_gb300 import workload as W
+from tests.gpu_helpers import VARIANTS, Pair, dev, host
+
+pytestmark = pytest.mark.gpu
+
+P = W.HASH_PRIME
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _lib():
+    sh.load_library()
+
+
+def test_bucket_hash_matches_oracle():
+    rng = np.random.default_rng(0)
+    keys = np.concatenate([
+        np.array([0, 1, 2, P - 1, P, P + 1, P + 2, 0xFFFFFFFD], np.uint32),
+        rng.integers(0, 0xFFFFFFFE, 20000, dtype=np.uint64).astype(np.uint32)])
+    for a, b, B in [(1, 0, 1), (1, 0, 7282), (P - 1, P - 1, 466034), (2, 3, 1 << 20),
+                    (int(rng.integers(1, P)), int(rng.integers(0, P)), 1398102)]:
+        t = sh.SlabHash(B, a, b, 1024)
+        got = host(t.buckets_of(dev(keys)))
+        want = np.array([hash_of(a, b, B, int(k)) for k in keys], np.uint32)
+        t.close()
+        assert (got == want).all(), (a, b, B, np.flatnonzero(got != want)[:5])
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_config1(variant):
+    """2^16 pairs, B = 7282, 2^16 searches at 50 % hit, 2^14 deletes (seed 0)."""
+    w = W.config1()
+    p = Pair(w.num_buckets, w.hash_a, w.hash_b, variant=variant, n_hint=len(w.keys))
+    try:
+        f = p.insert(w.keys, w.values)
+        assert f.sum() == 0
+        p.check_structure()
+        _, found = p.search(w.search.keys)
+        assert (found.astype(bool) == w.search.present).all()
+        d = p.delete(w.delete_keys)
+        assert d.all()
+        p.search(w.search.keys)
+        p.search(w.delete_keys)
+        p.check_structure()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 1000, 4097])
+def test_ragged_sizes(variant, n):
+    ks = W.KeyStream(n + 3)
+    keys = ks.take(n)
+    absent = ks.take(n)
+    a, b = W.hash_params(n)
+    for B in (1, 3, max(1, n // 9)):
+        p = Pair(B, a, b, variant=variant, n_hint=n)
+        try:
+            p.insert(keys, W.values_for(keys))
+            p.search(np.concatenate([keys, absent]))
+            p.delete(keys[::2])
+            p.search(keys)
+            p.check_structure()
+        finally:
+            p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("B,n", [(1, 2000), (2, 1500), (3, 46), (1, 15), (1, 16), (1, 30), (1, 31), (1, 45)])
+def test_long_chains_and_slab_boundaries(variant, B, n):
+    keys = W.KeyStream(B * 1000 + n).take(n)
+    a, b = W.hash_params(7)
+    p = Pair(B, a, b, variant=variant, n_hint=n)
+    try:
+        p.insert(keys, W.values_for(keys))
+        p.insert(keys[: n // 2], W.values_for(keys[: n // 2]) + np.uint32(1))  # replaces
+        p.search(keys)
+        p.delete(keys[1::3])
+        p.insert(keys[1::3], W.values_for(keys[1::3]))  # re-insert after delete: new slots
+        p.search(keys)
+        p.check_structure()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_value_equal_to_not_found_marker(variant):
+    key = np.array([0x61C88646, 5, 6], np.uint32)  # 0x61C88646 ^ 0x9E3779B9 = 0xFFFFFFFF
+    vals = W.values_for(key)
+    assert vals[0] == 0xFFFFFFFF
+    p = Pair(4, 3, 5, variant=variant)
+    try:
+        p.insert(key, vals)
+        v, f = p.search(key)
+        assert f.tolist() == [1, 1, 1] and v[0] == 0xFFFFFFFF
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_reserved_keys_are_refused(variant):
+    keys = np.array([10, 0xFFFFFFFE, 11, 0xFFFFFFFF, 12], np.uint32)
+    p = Pair(2, 9, 4, variant=variant)
+    try:
+        p.insert(keys, keys)
+        p.search(keys)
+        p.delete(keys)
+        ops = np.array([0, 1, 2, 0, 2], np.uint8)
+        p.mixed(ops, keys, keys)
+        p.check_structure(expect_flags=sh.SLAB_FLAG_RESERVED_KEY)
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_key_only_mode(variant):
+    ks = W.KeyStream(99)
+    keys = ks.take(5000)
+    absent = ks.take(2000)
+    a, b = W.hash_params(99)
+    p = Pair(200, a, b, variant=variant, key_only=True, n_hint=5000)
+    try:
+        p.insert(keys, None)
+        p.insert(keys[:100], None)  # already present
+        p.search(np.concatenate([keys, absent]))
+        p.delete(keys[::4])
+        p.search(keys)
+        rng = np.random.default_rng(3)
+        live = np.setdiff1d(keys, keys[::4])
+        mb, _ = W.mixed_batch(ks, live, 3000, (0.3, 0.3, 0.4), rng)
+        p.mixed(mb.ops, mb.keys, None)
+        p.check_structure()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_mixed_batches(variant):
+    """Sec. 6.3 workload at reduced scale: preload 2^16, then batches of 2^14 in each ratio."""
+    ks = W.KeyStream(5)
+    keys = ks.take(1 << 16)
+    a, b = W.hash_params(5)
+    B = W.buckets_for(1 << 16, 0.6)
+    p = Pair(B, a, b, variant=variant, n_hint=1 << 18)
+    rng = np.random.default_rng(5)
+    try:
+        p.insert(keys, W.values_for(keys))
+        live = keys
+        for ratios in W.CONFIG3_RATIOS:
+            for _ in range(3):
+                mb, live = W.mixed_batch(ks, live, 1 << 14, ratios, rng)
+                p.mixed(mb.ops, mb.keys, mb.values)
+        p.search(live[:5000])
+        p.check_structure()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_pool_exhaustion_reports_and_stays_consistent(variant):
+    """One memory block (1024 slabs) cannot hold 2^15 pairs in one bucket: some inserts
+    must fail with OUT_OF_SLABS; the rest land, and nothing hangs."""
+    keys = W.KeyStream(11).take(1 << 15)
+    p = Pair(1, 5, 6, pool_slabs=1024, variant=variant, iter_limit=1 << 20)
+    try:
+        res = host(p.g.mixed(torch.zeros(len(keys), dtype=torch.uint8, device="cuda"), dev(keys),
+                             dev(W.values_for(keys))))
+        rc, flags = p.g.status()
+        assert rc == sh.SLAB_ERR_OUT_OF_SLABS and flags & sh.SLAB_FLAG_OUT_OF_SLABS
+        ok = res == 1
+        assert 0 < ok.sum() <= 15 * 1025
+        fd = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
+        v = host(p.g.search(dev(keys), found=fd))
+        hit = fd.cpu().numpy().astype(bool)
+        assert (hit == ok).all()
+        assert (v[hit] == W.values_for(keys)[hit]).all()
+        tot = p.g.stats()
+        assert tot["live"] == ok.sum() and tot["prefix_violations"] == 0
+        # every allocated slab is linked; slabs freed by lost link races may stay free
+        assert tot["pool_allocated"] == tot["linked"] and 1000 <= tot["linked"] <= 1024
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_iteration_cap_ends_ops_with_a_status(variant):
+    """With a cap of one slab read per op, ops that must walk past the base slab stop
+    with ITER_LIMIT instead of finishing (B = 1, 64 keys need 5 slabs)."""
+    keys = W.KeyStream(12).take(64)
+    p = Pair(1, 5, 6, variant=variant, iter_limit=1)
+    try:
+        fd = torch.empty(64, dtype=torch.uint8, device="cuda")
+        p.g.insert(dev(keys), dev(W.values_for(keys)), fd)
+        rc, flags = p.g.status()
+        assert rc == sh.SLAB_ERR_ITER_LIMIT and flags == sh.SLAB_FLAG_ITER_LIMIT
+        tot = p.g.stats()
+        assert tot["live"] < 64 and tot["prefix_violations"] == 0
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("tpb,bps", [(32, 1), (128, 2), (512, 0), (1024, 1)])
+def test_launch_shapes(tpb, bps):
+    w = W.bulk_workload(20000, 0.8, 20000, 0.5, 5000, seed=4)
+    for variant in VARIANTS:
+        p = Pair(w.num_buckets, w.hash_a, w.hash_b, variant=variant, n_hint=20000,
+                 threads_per_block=tpb, blocks_per_sm=bps)
+        try:
+            p.insert(w.keys, w.values)
+            p.search(w.search.keys)
+            p.delete(w.delete_keys)
+            p.check_structure()
+        finally:
+            p.close()
+
+
+def test_side_stream():
+    w = W.bulk_workload(30000, 0.6, 30000, 0.5, 3000, seed=8)
+    s = torch.cuda.Stream()
+    p = Pair(w.num_buckets, w.hash_a, w.hash_b, n_hint=30000)
+    try:
+        with torch.cuda.stream(s):
+            p.insert(w.keys, w.values)
+            p.search(w.search.keys)
+        p.check_structure()
+    finally:
+        p.close()
+
+
+def test_slab_alloc_microbench_state():
+    """Sec. 5 SlabAlloc: n single-slab allocations give n distinct valid addresses,
+    the bitmaps mark exactly those units, and freeing them all clears every bit."""
+    from oracle import check_alloc
+    t = sh.SlabHash(8, 3, 4, pool_slabs=1 << 17)
+    try:
+        n = 100000
+        addrs = torch.empty(n, dtype=torch.int32, device="cuda")
+        t.configure(random_probes=64)
+        sh.slab_alloc_batch(t.handle, addrs)
+        rc, flags = t.status()
+        assert rc == sh.SLAB_OK, flags
+        a = host(addrs)
+        bm = host(t.bitmaps())
+        assert check_alloc(a, bm, t.info.num_memory_blocks) == (0, 0)
+        sh.slab_free_batch(t.handle, addrs)
+        assert (host(t.bitmaps()) == 0).all()
+        # more requests than units: the surplus fails with OUT_OF_SLABS, nothing hangs
+        m = (1 << 17) + 5000
+        addrs = torch.empty(m, dtype=torch.int32, device="cuda")
+        sh.slab_alloc_batch(t.handle, addrs)
+        rc, flags = t.status()
+        assert rc == sh.SLAB_ERR_OUT_OF_SLABS
+        a = host(addrs)
+        good = a != 0xFFFFFFFF
+        assert good.sum() <= 1 << 17
+        assert check_alloc(a[good], host(t.bitmaps()), t.info.num_memory_blocks) == (0, 0)
+    finally:
+        t.close()
