@@ -1,0 +1,430 @@
+"""Benchmark of the slab hash hot path on GB300.
+
+One step = one pass of the whole hot path over one batch of the 2^22-key bulk
+workload (Sec. 6.1, beta = 0.6, 50 % search hits) followed by one concurrent
+batch (Sec. 6.3): reset the table, bulk-build 2^22 pairs, search 2^22 keys,
+delete 2^20 keys, run 2^20 mixed ops (insert/delete/search = 0.2/0.2/0.6).
+Inputs are resident in HBM before the timed region; L2 is flushed (a 256 MiB
+write) before every step. Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --sweep   # extra lines: beta sweep, hit rates, SlabAlloc, probes
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1710_11246_gb300 import workload as W  # noqa: E402
+
+METRIC = "Mops/s search/insert/delete/mixed at 2^22 keys; % of random-128B-line roofline"
+N_KEYS = 1 << 22
+N_SEARCH = 1 << 22
+N_DELETE = 1 << 20
+N_MIXED = 1 << 20
+BETA = 0.6
+HIT = 0.5
+MIXED_RATIOS = (0.2, 0.2, 0.6)
+POOL_SLABS = 1 << 20
+OPS_PER_STEP = N_KEYS + N_SEARCH + N_DELETE + N_MIXED
+PHASES = ("reset", "build", "search", "delete", "mixed")
+
+
+def make_step_inputs(seed: int = 0):
+    """The step's batches (deterministic for a seed)."""
+    w = W.config2(BETA, HIT, seed)
+    stream = W.KeyStream(seed)
+    stream.take(N_KEYS + (N_SEARCH - int(round(N_SEARCH * HIT))))  # skip keys the bulk workload used
+    rng = np.random.default_rng([seed, 0x3333])
+    live = np.setdiff1d(w.keys, w.delete_keys, assume_unique=True)
+    mb, _ = W.mixed_batch(stream, live, N_MIXED, MIXED_RATIOS, rng)
+    return w, mb
+
+
+def config_dict(extra=None):
+    d = {"workload": f"bulk build 2^22 pairs (beta={BETA}, B=ceil(n/(15*beta))), search 2^22 at "
+                     f"{int(HIT * 100)}% hit, delete 2^20, mixed 2^20 ops {MIXED_RATIOS}",
+         "num_keys": N_KEYS, "beta": BETA, "num_buckets": W.buckets_for(N_KEYS, BETA),
+         "ops_per_step": OPS_PER_STEP, "l2": "flushed before every step (256 MiB write)",
+         "parallelism": "replicas"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------- CPU oracle
+def run_oracle_step(w, mb):
+    """One step on the CPU oracle; returns (seconds, lines touched per phase)."""
+    from oracle import OracleTable
+    t0 = time.perf_counter()
+    o = OracleTable(w.num_buckets, w.hash_a, w.hash_b)
+    lines = {}
+    o.insert(w.keys, w.values)
+    lines["build"] = o.lines
+    o.lines = 0
+    o.search(w.search.keys)
+    lines["search"] = o.lines
+    o.lines = 0
+    o.delete(w.delete_keys)
+    lines["delete"] = o.lines
+    o.lines = 0
+    o.mixed(mb.ops, mb.keys, mb.values)
+    lines["mixed"] = o.lines
+    o.close()
+    return time.perf_counter() - t0, lines
+
+
+def cpu_baseline(w, mb, budget_s: float = 10.0):
+    """The oracle as it stands, single-threaded, on whole steps of the same workload."""
+    times, lines = [], None
+    t_start = time.perf_counter()
+    while not times or (time.perf_counter() - t_start < budget_s and len(times) < 5):
+        dt, lines = run_oracle_step(w, mb)
+        times.append(dt)
+    v = OPS_PER_STEP * len(times) / sum(times) / 1e6
+    return {"value": round(v, 3), "unit": "Mops/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} whole step(s) of the workload ({OPS_PER_STEP} ops each), "
+                      f"plain C oracle, one thread"}, lines, times
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        busy = [num(r[0]) for r in self.rows if num(r[8]) and num(r[8]) > 0 and num(r[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(busy or sm) if sm else None,
+                "sm_max_mhz": num(self.rows[0][1]), "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max((num(r[2]) or 0) for r in self.rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def gpu_arm(args, rank, world, device):
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+
+    sh.load_library()
+    w, mb = make_step_inputs(args.seed)
+    dev = sh.as_device_u32
+    t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, POOL_SLABS)
+    if args.variant == "direct":
+        t.configure(variant=sh.SLAB_VARIANT_DIRECT)
+    if args.threads_per_block:
+        t.configure(threads_per_block=args.threads_per_block)
+    if args.blocks_per_sm is not None:
+        t.configure(blocks_per_sm=args.blocks_per_sm)
+    stream = torch.cuda.Stream()
+    h = t.handle
+
+    # device-resident inputs and outputs
+    k_build, v_build = dev(w.keys), dev(w.values)
+    k_search = dev(w.search.keys)
+    k_del = dev(w.delete_keys)
+    m_ops = torch.from_numpy(mb.ops).to(device)
+    m_keys, m_vals = dev(mb.keys), dev(mb.values)
+    o_search = torch.empty(N_SEARCH, dtype=torch.int32, device=device)
+    f_search = torch.empty(N_SEARCH, dtype=torch.uint8, device=device)
+    f_del = torch.empty(N_DELETE, dtype=torch.uint8, device=device)
+    o_mixed = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+    f_mixed = torch.empty(N_MIXED, dtype=torch.uint8, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    torch.cuda.synchronize()
+
+    def step(evs):
+        evs[0].record(stream)
+        sh.slab_reset(h, stream)
+        evs[1].record(stream)
+        sh.slab_insert_batch(h, k_build, v_build, None, stream=stream)
+        evs[2].record(stream)
+        sh.slab_search_batch(h, k_search, o_search, f_search, stream=stream)
+        evs[3].record(stream)
+        sh.slab_delete_batch(h, k_del, f_del, stream=stream)
+        evs[4].record(stream)
+        sh.slab_mixed_batch(h, m_ops, m_keys, m_vals, o_mixed, f_mixed, stream=stream)
+        evs[5].record(stream)
+
+    def new_events():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(new_events())
+    torch.cuda.synchronize()
+    rc, flags = t.status(stream)
+    if rc != sh.SLAB_OK:
+        raise RuntimeError(f"device status after warm-up: rc={rc} flags={flags}")
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    all_evs = []
+    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ
+                      else int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        time.sleep(0.25)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.zero_()
+                evs = new_events()
+                step(evs)
+                all_evs.append(evs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        time.sleep(0.25)
+    if world > 1:
+        torch.distributed.barrier()
+    rc, flags = t.status(stream)
+    if rc != sh.SLAB_OK:
+        raise RuntimeError(f"device status after timed steps: rc={rc} flags={flags}")
+
+    per_phase = {p: [] for p in PHASES}
+    step_ms = []
+    for evs in all_evs:
+        for i, p in enumerate(PHASES):
+            per_phase[p].append(evs[i].elapsed_time(evs[i + 1]))
+        step_ms.append(evs[0].elapsed_time(evs[5]))
+    total_ms = sum(step_ms)
+    if world > 1:
+        x = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(x.item())
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if rank == 0 or True:
+        e2e = e2e_arm(args, t, w, mb, device, stream)
+    res = dict(per_phase=per_phase, step_ms=step_ms, total_ms=total_ms, wall=wall, clocks=clk.summary(),
+               e2e=e2e, table=t, w=w, mb=mb)
+    return res
+
+
+def e2e_arm(args, t, w, mb, device, stream):
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    h = t.handle
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32 if a.dtype == np.uint32 else a.dtype)).pin_memory()  # noqa: E731
+    hk, hv, hs, hd = pin(w.keys), pin(w.values), pin(w.search.keys), pin(w.delete_keys)
+    hops, hmk, hmv = pin(mb.ops), pin(mb.keys), pin(mb.values)
+    outs = [torch.empty(N_SEARCH, dtype=torch.int32).pin_memory(), torch.empty(N_SEARCH, dtype=torch.uint8).pin_memory(),
+            torch.empty(N_DELETE, dtype=torch.uint8).pin_memory(), torch.empty(N_MIXED, dtype=torch.int32).pin_memory(),
+            torch.empty(N_MIXED, dtype=torch.uint8).pin_memory()]
+    d = {n: torch.empty_like(x, device=device) for n, x in
+         dict(k=hk, v=hv, s=hs, dl=hd, ops=hops, mk=hmk, mv=hmv).items()}
+    dout = [torch.empty_like(x, device=device) for x in outs]
+    h2d = sum(x.numel() * x.element_size() for x in (hk, hv, hs, hd, hops, hmk, hmv))
+    d2h = sum(x.numel() * x.element_size() for x in outs)
+
+    def one():
+        for n, x in dict(k=hk, v=hv, s=hs, dl=hd, ops=hops, mk=hmk, mv=hmv).items():
+            d[n].copy_(x, non_blocking=True)
+        sh.slab_reset(h, stream)
+        sh.slab_insert_batch(h, d["k"], d["v"], None, stream=stream)
+        sh.slab_search_batch(h, d["s"], dout[0], dout[1], stream=stream)
+        sh.slab_delete_batch(h, d["dl"], dout[2], stream=stream)
+        sh.slab_mixed_batch(h, d["ops"], d["mk"], d["mv"], dout[3], dout[4], stream=stream)
+        for o, x in zip(outs, dout):
+            o.copy_(x, non_blocking=True)
+
+    steps = max(3, min(args.steps, 20))
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            one()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": round(OPS_PER_STEP / (ms * 1e3), 1), "unit": "Mops/s", "ms_per_step": round(ms, 4),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24):
+    """Best random 128-byte-line read rate (lines/s) at a footprint, over lines in flight."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    lines = footprint_bytes // 128
+    buf = torch.zeros(lines * 32, dtype=torch.int32, device=device)
+    sink = torch.zeros(1, dtype=torch.int32, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    best = (0.0, None)
+    for lif in (4, 8, 16):
+        for tpb in (256, 512):
+            ts = []
+            for rep in range(4):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                sh.slab_probe_random_lines(buf, lines, n_reads, rep + 1, lif, tpb, sink)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            rate = n_reads / (min(ts[1:]) * 1e-3)
+            if rate > best[0]:
+                best = (rate, {"lines_in_flight": lif, "threads_per_block": tpb})
+    del buf
+    return best
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="staged", choices=["staged", "direct"])
+    ap.add_argument("--threads-per-block", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+
+    r = gpu_arm(args, rank, world, device)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    ms_step = r["total_ms"] / args.steps
+    value = OPS_PER_STEP * world / (ms_step * 1e3)  # Mops/s over all ranks
+    mean = {p: statistics.fmean(v) for p, v in r["per_phase"].items()}
+    ops = {"build": N_KEYS, "search": N_SEARCH, "delete": N_DELETE, "mixed": N_MIXED}
+    per_op = {p: round(ops[p] / (mean[p] * 1e3), 1) for p in ops}
+
+    cpu = None
+    lines = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, lines, _ = cpu_baseline(r["w"], r["mb"])
+
+    # roofline of the dominant kernel: algorithmic bytes = 128 B per slab the op must
+    # read (oracle line count of this workload) + its own input/output bytes
+    io = {"build": 8, "search": 4 + 4 + 1, "delete": 4 + 1, "mixed": 1 + 4 + 4 + 4 + 1}
+    dom = max(ops, key=lambda p: mean[p])
+    roof = None
+    rl = None
+    if lines is not None:
+        alg = {p: 128 * lines[p] + io[p] * ops[p] for p in ops}
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        achieved = alg[dom] / (mean[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{dom} ({args.variant}_kernel)", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "lines_per_op": {p: round(lines[p] / ops[p], 4) for p in ops}}
+        if not args.no_probe:
+            fp = r["table"].info.num_buckets * 128
+            rate, cfg = random_line_probe(device, fp)
+            rate_big, cfg_big = random_line_probe(device, 4 << 30)
+            rl = {"footprint_bytes": fp, "glines_per_s": round(rate / 1e9, 3), "probe": cfg,
+                  "glines_per_s_4GiB": round(rate_big / 1e9, 3),
+                  "per_phase_frac": {p: round(lines[p] / (mean[p] * 1e-3) / rate, 4) for p in ops}}
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_dict({"variant": args.variant}),
+        "per_op_mops": per_op, "phase_ms": {p: round(mean[p], 4) for p in PHASES},
+        "roofline": roof, "random_line_roofline": rl, "cpu_baseline": cpu,
+        "e2e": r["e2e"], "gpu_launches": 5 * args.steps, "clocks": r["clocks"],
+    }
+    print(json.dumps(out))
+    r["table"].close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The oracle as it stands on the host cores, whole steps of the same workload."""
+    if rank != 0:
+        return
+    w, mb = make_step_inputs(args.seed)
+    for _ in range(args.warmup):
+        run_oracle_step(w, mb)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = run_oracle_step(w, mb)
+        times.append(dt)
+    total = sum(times)
+    value = OPS_PER_STEP * args.steps / total / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mops/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": config_dict(),
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 3), "unit": "Mops/s",
+                            "sample": f"whole steps ({OPS_PER_STEP} ops each), plain C oracle, one thread"},
+           "e2e": {"value": round(value, 3), "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

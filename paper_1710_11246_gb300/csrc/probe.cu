@@ -26,26 +26,32 @@ __device__ __forceinline__ uint64_t pick(uint64_t r, uint64_t seed, uint64_t n) 
     return ((uint64_t)mix(r ^ (seed << 40)) * n) >> 32;
 }
 
+// Each warp takes 32 reads at a time: lane j draws the line of read j, then the
+// warp reads the 32 lines one after another (32 lanes x 4 bytes each), L lines
+// issued before any is consumed.
 template <int L>
 __global__ void probe_lines_kernel(const uint32_t* __restrict__ buf, uint64_t footprint, uint64_t n_reads,
                                    uint32_t seed, uint32_t* sink) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t per = (n_reads + nwarps - 1) / nwarps;
-    const uint64_t begin = warp * per;
-    const uint64_t end = min(begin + per, n_reads);
+    const uint64_t groups = (n_reads + 31) / 32;
     uint32_t acc = 0;
-    for (uint64_t i = begin; i < end; i += L) {
-        uint32_t v[L];
+    for (uint64_t g = warp; g < groups; g += nwarps) {
+        const uint64_t r = g * 32 + lane;
+        const uint32_t my_line = (uint32_t)pick(r, seed, footprint);
+        const uint32_t valid = __ballot_sync(0xFFFFFFFFu, r < n_reads);
 #pragma unroll
-        for (int j = 0; j < L; ++j) {
-            const uint64_t r = i + j;
-            const uint64_t line = pick(r, seed, footprint);
-            v[j] = r < end ? __ldcg(buf + line * 32 + lane) : 0u;
+        for (int j0 = 0; j0 < 32; j0 += L) {
+            uint32_t v[L];
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+                const uint32_t line = __shfl_sync(0xFFFFFFFFu, my_line, j0 + j);
+                v[j] = ((valid >> (j0 + j)) & 1u) ? __ldcg(buf + (uint64_t)line * 32 + lane) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < L; ++j) acc ^= v[j];
         }
-#pragma unroll
-        for (int j = 0; j < L; ++j) acc ^= v[j];
     }
     for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if (lane == 0) atomicXor(sink, acc);

@@ -1,0 +1,259 @@
+// The GB300 kernel family for slab-hash batches: warp-cooperative work sharing
+// (Sec. 4.1) with the slab reads moved off the critical path.
+//
+// Each warp walks tiles of 32 ops (one per lane) in a persistent grid, as a
+// three-stage pipeline:
+//   tile t+2  its keys, values and op codes are being loaded into registers;
+//   tile t+1  its keys are hashed and its 32 base slabs are in flight into one
+//             half of the warp's shared-memory stage (cp.async, 16 bytes per
+//             lane, 4 slabs per warp instruction);
+//   tile t    is served from the other half.
+// Serving a tile is the WCWS loop of Fig. "alg:search": the warp takes the queued
+// ops in lane order; for each one it reads the op's slab coalesced (word `lane`
+// per lane, here from the stage), broadcasts the op's key by shuffle and finds
+// matching or empty key lanes by ballot. The ballot word is parked in shared
+// memory and the source lane then acts on it: it reads the value (search),
+// writes the tombstone (delete) or issues the 64-bit CAS of the pair (replace).
+// All source lanes act in the same instructions, so the 32 CASes of a tile are in
+// flight together and their results are checked once. Ops that must follow a
+// next pointer, or whose CAS lost a race, restage just their slabs and go round
+// again; a full list grows through SlabAlloc exactly as in the paper.
+#pragma once
+#include "slab_device.cuh"
+#include "slab_wcws.cuh"
+
+namespace slab {
+
+constexpr uint32_t kTileWords = 32u * kWordsPerSlab;             // one slab per lane: 4 KB
+constexpr uint32_t kStagedWordsPerWarp = 2u * kTileWords + 32u;  // two tile buffers + 32 ballot words
+constexpr uint32_t kNoOpCode = 0xFFu;
+
+__device__ __forceinline__ void cp_async_16(uint32_t smem_addr, const void* gptr) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage position of word w of the slab in slot s. The 16-byte chunks of a slot
+// are rotated by XOR with (s mod 8): a warp reading word `lane` of one slot hits
+// 32 distinct banks, and 32 lanes each reading one word of their own slot hit at
+// most 4 lanes per bank.
+__device__ __forceinline__ uint32_t swz(uint32_t s, uint32_t w) {
+    return s * 32u + ((((w >> 2) ^ (s & 7u)) << 2) | (w & 3u));
+}
+
+// Copy, for every lane s in `mask`, the slab with unified index shfl(u, s)
+// (base slab b -> b, pool unit a -> B + a) into slot s of the stage at byte
+// address `stage`: lanes 8g..8g+7 move one slab as eight 16-byte pieces.
+__device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, uint32_t u, uint32_t mask,
+                                            uint32_t lane) {
+    const uint32_t c = lane & 7u;
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) {
+        const uint32_t s = 4u * j + (lane >> 3);
+        const uint32_t us = __shfl_sync(kFull, u, s);
+        if ((mask >> s) & 1u)
+            cp_async_16(stage + (s * 32u + ((c ^ (s & 7u)) << 2)) * 4u, T.slabs + (uint64_t)us * kWordsPerSlab + c * 4u);
+    }
+}
+
+template <int kKind, bool kKeyOnly>
+__global__ void staged_kernel(TableView T, BatchArgs A) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
+    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    const uint32_t lane = lane_id();
+    uint32_t* wsm = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp;
+    uint32_t* ballots = wsm + 2u * kTileWords;
+    const uint32_t wsm_s = (uint32_t)__cvta_generic_to_shared(wsm);
+    const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t ntiles = (A.n + 31u) / 32u;
+    uint32_t t = warp_gid;
+    if (t >= ntiles) return;  // warp-uniform
+
+    // word `lane` of slot s sits at s * 32 + off[s & 7]
+    uint32_t off[8];
+#pragma unroll
+    for (uint32_t j = 0; j < 8; ++j) off[j] = (((lane >> 2) ^ j) << 2) | (lane & 3u);
+
+    AllocCtx ac{kNoBlock, 0u, 0u};
+
+    auto fetch = [&](uint32_t tt, uint32_t& k, uint32_t& v, uint32_t& o) {
+        const uint32_t i = tt * 32u + lane;
+        const bool has = tt < ntiles && i < A.n;
+        o = kNoOpCode;
+        k = 0u;
+        v = 0u;
+        if (has) {
+            o = kKind == kKindMixed ? ld_stream_u8(A.ops + i) : fixed_op<kKind>();
+            k = ld_stream(A.keys + i);
+            if (kNeedsValue && A.values) v = ld_stream(A.values + i);
+        }
+    };
+    auto walks = [](uint32_t k, uint32_t o) { return o <= kOpSearch && k < kTombstone; };
+
+    // prologue: tile t staged into buffer 0, tile t + nwarps loading
+    uint32_t ck, cv, co;
+    fetch(t, ck, cv, co);
+    uint32_t cb = walks(ck, co) ? bucket_of(T, ck) : 0u;
+    stage_slabs(T, wsm_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
+    cp_async_commit();
+    uint32_t nk, nv, no;
+    fetch(t + nwarps, nk, nv, no);
+    uint32_t parity = 0;
+
+    for (; t < ntiles; t += nwarps) {
+        // (1) next tile: hash its keys and start staging its base slabs
+        const bool nwalk = walks(nk, no);
+        const uint32_t nb = nwalk ? bucket_of(T, nk) : 0u;
+        stage_slabs(T, wsm_s + (parity ^ 1u) * kTileWords * 4u, nb, __ballot_sync(kFull, nwalk), lane);
+        cp_async_commit();
+        // (2) the tile after it: start its loads
+        uint32_t mk, mv, mo;
+        fetch(t + 2u * nwarps, mk, mv, mo);
+        // (3) this tile's base slabs were committed one tile ago
+        cp_async_wait<1>();
+        __syncwarp();
+
+        // (4) serve this tile
+        const uint32_t* buf = wsm + parity * kTileWords;
+        const uint32_t buf_s = wsm_s + parity * kTileWords * 4u;
+        const uint32_t idx = t * 32u + lane;
+        bool pending = walks(ck, co);
+        if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
+        uint32_t res = default_result(co), fnd = 0, cur = kEmptyKey, rounds = 0;
+        bool first = true;
+        for (;;) {
+            const uint32_t pend = __ballot_sync(kFull, pending);
+            if (!pend) break;
+            const uint32_t u = cur == kEmptyKey ? cb : T.num_buckets + cur;
+            if (!first) {  // restage only the ops that moved on or must retry
+                stage_slabs(T, buf_s, u, pend, lane);
+                cp_async_commit();
+                cp_async_wait<0>();
+                __syncwarp();
+            }
+            // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10)
+            auto step = [&](uint32_t s, uint32_t data) {
+                const uint32_t skey = __shfl_sync(kFull, ck, s);
+                bool pred;
+                if constexpr (kKind == kKindInsert) {
+                    pred = data == skey || data == kEmptyKey;
+                } else if constexpr (kKind == kKindMixed) {
+                    const uint32_t sop = __shfl_sync(kFull, co, s);
+                    pred = data == skey || (sop == kOpInsert && data == kEmptyKey);
+                } else {
+                    pred = data == skey;
+                }
+                const uint32_t mm = __ballot_sync(kFull, pred);
+                if (lane == 0) ballots[s] = mm;
+            };
+            if (first) {
+#pragma unroll
+                for (uint32_t s = 0; s < 32; ++s)
+                    if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
+            } else {
+                for (uint32_t q = pend; q; q &= q - 1u) {
+                    const uint32_t s = (uint32_t)(__ffs(q) - 1);
+                    step(s, buf[swz(s, lane)]);
+                }
+            }
+            __syncwarp();
+
+            // the source lanes act on their ballots (Sec. 4.3)
+            const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
+            uint32_t* gslab = T.slabs + (uint64_t)u * kWordsPerSlab;
+            bool cas_wait = false, cas_new = false, need_slab = false;
+            unsigned long long cas_exp = 0, cas_got = 0;
+            if (pending) {
+                if (m) {
+                    const uint32_t d = (uint32_t)(__ffs(m) - 1);
+                    if (co == kOpSearch) {
+                        res = kKeyOnly ? 0u : buf[swz(lane, d + 1u)];
+                        fnd = 1u;
+                        pending = false;
+                    } else if (co == kOpDelete) {
+                        st_relaxed(gslab + d, kTombstone);
+                        res = 1u;
+                        fnd = 1u;
+                        pending = false;
+                    } else if constexpr (kKeyOnly) {
+                        if (buf[swz(lane, d)] == ck) {  // already present
+                            res = 0u;
+                            fnd = 1u;
+                            pending = false;
+                        } else {
+                            cas_exp = kEmptyKey;
+                            cas_got = atomicCAS(gslab + d, kEmptyKey, ck);
+                            cas_wait = true;
+                            cas_new = true;
+                        }
+                    } else {
+                        const uint2 pr = *reinterpret_cast<const uint2*>(buf + swz(lane, d));
+                        cas_exp = pack_pair(pr.x, pr.y);
+                        cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
+                                            pack_pair(ck, cv));
+                        cas_wait = true;
+                        cas_new = pr.x == kEmptyKey;
+                    }
+                } else {
+                    const uint32_t nx = buf[swz(lane, kAddressLane)];
+                    if (nx == kEmptyKey) {
+                        if (co == kOpInsert) need_slab = true;
+                        else pending = false;  // end of the list: not found
+                    } else if (valid_next(T, nx)) {
+                        cur = nx;
+                    } else {
+                        set_flag(T, kFlagBadPointer);
+                        pending = false;
+                    }
+                }
+            }
+            if (cas_wait && cas_got == cas_exp) {  // otherwise: restage this slab and retry
+                fnd = cas_new ? 0u : 1u;
+                res = cas_new ? 1u : 0u;
+                pending = false;
+            }
+            // full lists grow by one slab each (warp-wide SlabAlloc, Sec. 5)
+            for (uint32_t q = __ballot_sync(kFull, need_slab); q; q &= q - 1u) {
+                const int s = __ffs(q) - 1;
+                uint32_t* ps = reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)gslab, s));
+                const uint32_t nx = grow_list(T, ac, warp_gid, ps, s);
+                if ((int)lane == s) {
+                    if (nx == kAllocFailed) {
+                        set_flag(T, kFlagOutOfSlabs);
+                        pending = false;
+                    } else if (valid_next(T, nx)) {
+                        cur = nx;
+                    } else {
+                        set_flag(T, kFlagBadPointer);
+                        pending = false;
+                    }
+                }
+            }
+            if (pending && ++rounds >= T.iter_limit) {
+                set_flag(T, kFlagIterLimit);
+                pending = false;
+            }
+            first = false;
+            __syncwarp();
+        }
+        if (idx < A.n) {
+            if (A.results) A.results[idx] = res;
+            if (A.found) A.found[idx] = (uint8_t)fnd;
+        }
+
+        // (5) rotate the pipeline
+        ck = nk; cv = nv; co = no; cb = nb;
+        nk = mk; nv = mv; no = mo;
+        parity ^= 1u;
+        __syncwarp();
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace slab

@@ -1,17 +1,8 @@
-// Warp-cooperative work sharing (WCWS, Sec. 4.1) over slab lists: the two
-// kernel families that serve search / replace / delete / mixed batches.
-//
-//   direct_kernel  the loop of Fig. "alg:search" as written: one op per lane,
-//                  the warp serves its queue one op at a time, each step reads
-//                  the current slab from global memory.
-//   staged_kernel  the same per-op WCWS step, reorganised for sm_103a memory
-//                  latency: every lane keeps one pending op in a persistent
-//                  window; each round the warp copies all pending ops' current
-//                  slabs into its shared-memory stage with cp.async (up to 32
-//                  independent 128-byte lines in flight per warp), then serves
-//                  the ops one at a time from the stage. Insert CASes are issued
-//                  without waiting and checked at the end of the round; a lane
-//                  whose op finished takes the next op of the warp's range.
+// Warp-cooperative work sharing (WCWS, Sec. 4.1) over slab lists, in the form of
+// Fig. "alg:search": one op per lane, the warp serves its queue one op at a time,
+// each step reads the source lane's current slab from global memory. This is the
+// paper-structured kernel family (direct_kernel); slab_staged.cuh holds the
+// pipelined GB300 family built from the same step.
 #pragma once
 #include "slab_device.cuh"
 
@@ -201,169 +192,6 @@ __global__ void direct_kernel(TableView T, BatchArgs A) {
             if (A.results) A.results[idx] = res;
             if (A.found) A.found[idx] = (uint8_t)fnd;
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// GB300 kernel: persistent per-warp op window with shared-memory slab staging.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async_16(uint32_t smem_addr, const void* gptr) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr), "l"(gptr) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-constexpr uint32_t kNoOp = 0xFFFFFFFFu;
-constexpr uint32_t kStageWordsPerWarp = 32u * kWordsPerSlab;  // 32 slabs = 4 KB
-
-template <int kKind, bool kKeyOnly>
-__global__ void staged_kernel(TableView T, BatchArgs A, uint32_t ops_per_warp) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    const uint32_t lane = lane_id();
-    const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint32_t* stage = smem + (threadIdx.x >> 5) * kStageWordsPerWarp;
-    const uint32_t stage_base = (uint32_t)__cvta_generic_to_shared(stage);
-
-    // This warp's contiguous share of the batch.
-    const uint64_t begin64 = (uint64_t)warp_gid * ops_per_warp;
-    const uint32_t begin = (uint32_t)min(begin64, (uint64_t)A.n);
-    const uint32_t end = (uint32_t)min(begin64 + ops_per_warp, (uint64_t)A.n);
-    uint32_t next = begin;
-
-    AllocCtx ac{kNoBlock, 0u, 0u};
-    // Per-lane op state.
-    uint32_t my = kNoOp, key = 0, value = 0, op = 0, bucket = 0, cur = kEmptyKey, rounds = 0;
-    uint32_t res = 0, fnd = 0;
-    bool done = false, cas_wait = false, cas_new = false;
-    unsigned long long cas_exp = 0, cas_got = 0;
-    uint32_t* myp = nullptr;
-    const uint32_t lt_mask = (1u << lane) - 1u;
-
-    for (;;) {
-        // Refill: lanes without an op take the next ops of the range, in lane order.
-        const uint32_t need = __ballot_sync(kFull, my == kNoOp);
-        if (need && next < end) {
-            const uint32_t i = next + __popc(need & lt_mask);
-            if (my == kNoOp && i < end) {
-                my = i;
-                op = fixed_op<kKind>();
-                if constexpr (kKind == kKindMixed) op = ld_stream_u8(A.ops + i);
-                key = ld_stream(A.keys + i);
-                if ((kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly && A.values)
-                    value = ld_stream(A.values + i);
-                res = default_result(op);
-                fnd = 0;
-                cur = kEmptyKey;
-                rounds = 0;
-                if (op > kOpSearch) {
-                    res = 0;
-                    done = true;
-                } else if (key >= kTombstone) {
-                    set_flag(T, kFlagReserved);
-                    done = true;
-                } else {
-                    bucket = bucket_of(T, key);
-                }
-            }
-            next = min(next + (uint32_t)__popc(need), end);
-        }
-        const uint32_t pend = __ballot_sync(kFull, my != kNoOp && !done);
-
-        if (pend) {
-            // Stage every pending op's current slab: 8 lanes x 16 bytes per slab,
-            // 4 slabs per warp instruction.
-            const uint32_t u = cur == kEmptyKey ? bucket : T.num_buckets + cur;
-            myp = T.slabs + (uint64_t)u * kWordsPerSlab;
-            __syncwarp();
-#pragma unroll
-            for (uint32_t j = 0; j < 8; ++j) {
-                const uint32_t s = 4u * j + (lane >> 3);
-                const uint32_t us = __shfl_sync(kFull, u, s);
-                if ((pend >> s) & 1u) {
-                    const uint32_t c = lane & 7u;
-                    cp_async_16(stage_base + (s * kWordsPerSlab + c * 4u) * 4u,
-                                T.slabs + (uint64_t)us * kWordsPerSlab + c * 4u);
-                }
-            }
-            cp_async_wait_all();
-            __syncwarp();
-
-            // Serve the window's ops one at a time (WCWS).
-            uint32_t q = pend;
-            while (q) {
-                const int s = __ffs(q) - 1;
-                q &= q - 1u;
-                const uint32_t data = stage[s * kWordsPerSlab + lane];
-                const uint32_t skey = __shfl_sync(kFull, key, s);
-                const uint32_t sop = kKind == kKindMixed ? __shfl_sync(kFull, op, s) : fixed_op<kKind>();
-                const Outcome o = examine<kKeyOnly>(data, sop, skey);
-                const bool me = (int)lane == s;
-                if (o.kind == kResolved) {
-                    if (me) { res = o.a; fnd = o.b; done = true; }
-                } else if (o.kind == kAdvance) {
-                    if (me) {
-                        if (valid_next(T, o.a)) {
-                            cur = o.a;
-                        } else {
-                            set_flag(T, kFlagBadPointer);
-                            done = true;
-                        }
-                    }
-                } else if (o.kind == kMarkDead) {
-                    if (me) {
-                        st_relaxed(myp + o.a, kTombstone);
-                        res = 1u; fnd = 1u; done = true;
-                    }
-                } else if (o.kind == kClaim) {
-                    if (me) {  // issue now, check after the round
-                        if constexpr (kKeyOnly) {
-                            cas_exp = kEmptyKey;
-                            cas_got = atomicCAS(myp + o.a, kEmptyKey, key);
-                        } else {
-                            cas_exp = pack_pair(o.b, o.c);
-                            cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(myp + o.a),
-                                                cas_exp, pack_pair(key, value));
-                        }
-                        cas_wait = true;
-                        cas_new = o.b == kEmptyKey;
-                    }
-                } else {  // kNeedSlab
-                    uint32_t* ps = reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)myp, s));
-                    const uint32_t nx = grow_list(T, ac, warp_gid, ps, s);
-                    if (me) {
-                        if (nx == kAllocFailed) {
-                            set_flag(T, kFlagOutOfSlabs);
-                            done = true;
-                        } else if (valid_next(T, nx)) {
-                            cur = nx;
-                        } else {
-                            set_flag(T, kFlagBadPointer);
-                            done = true;
-                        }
-                    }
-                }
-            }
-            if (cas_wait) {
-                cas_wait = false;
-                if (cas_got == cas_exp) {
-                    fnd = cas_new ? 0u : 1u;
-                    res = cas_new ? 1u : 0u;
-                    done = true;
-                }  // else: retry this slab next round
-            }
-            if (my != kNoOp && !done && ++rounds >= T.iter_limit) {
-                set_flag(T, kFlagIterLimit);
-                done = true;
-            }
-        }
-        if (done) {
-            if (A.results) A.results[my] = res;
-            if (A.found) A.found[my] = (uint8_t)fnd;
-            my = kNoOp;
-            done = false;
-        }
-        if (!pend && next >= end) break;  // nothing pending and the range is used up
     }
 }
 

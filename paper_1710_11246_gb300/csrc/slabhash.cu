@@ -10,6 +10,7 @@
 
 #include "../../include/slabhash.h"
 #include "slab_device.cuh"
+#include "slab_staged.cuh"
 #include "slab_wcws.cuh"
 
 using namespace slab;
@@ -70,8 +71,8 @@ bool valid_config(const slab_config& c) {
     return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
            c.threads_per_block >= 32 && c.threads_per_block <= 1024 && c.threads_per_block % 32 == 0 &&
            c.blocks_per_sm >= 0 && c.blocks_per_sm <= 64 && c.iter_limit >= 1 && c.random_probes <= (1u << 20) &&
-           // staged kernels hold 4 KB of shared memory per warp
-           (c.variant != SLAB_VARIANT_STAGED || c.threads_per_block / 32 * 4096 <= 227 * 1024);
+           // staged kernels hold two 4 KB tile buffers per warp
+           (c.variant != SLAB_VARIANT_STAGED || c.threads_per_block / 32 * kStagedWordsPerWarp * 4 <= 227 * 1024);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -228,7 +229,7 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
         k<<<grid, tpb, 0, S(stream)>>>(T, a);
     } else {
         auto k = staged_kernel<kKind, kKeyOnly>;
-        const size_t smem = (size_t)wpb * kStageWordsPerWarp * 4;
+        const size_t smem = (size_t)wpb * kStagedWordsPerWarp * 4;
         if ((int)smem > t->max_smem_optin) return SLAB_ERR_INVALID_ARG;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -236,12 +237,10 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
         int bps = t->cfg.blocks_per_sm;
         if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, tpb, smem) != cudaSuccess)
             return SLAB_ERR_CUDA;
-        const uint64_t warps_wanted = (a.n + 31u) / 32u;
-        const uint64_t want = (warps_wanted + wpb - 1) / wpb;
+        const uint64_t tiles = (a.n + 31u) / 32u;
+        const uint64_t want = (tiles + wpb - 1) / wpb;
         const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
-        const uint64_t warps = grid * wpb;
-        const uint32_t per_warp = (uint32_t)((a.n + warps - 1) / warps);
-        k<<<(uint32_t)grid, tpb, smem, S(stream)>>>(T, a, per_warp);
+        k<<<(uint32_t)grid, tpb, smem, S(stream)>>>(T, a);
     }
     return launch_rc();
 }
@@ -317,7 +316,7 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     }
     t->device_bytes = slab_bytes + bitmap_bytes + 128;
     t->cfg.variant = SLAB_VARIANT_STAGED;
-    t->cfg.threads_per_block = 256;
+    t->cfg.threads_per_block = 128;
     t->cfg.blocks_per_sm = 0;
     t->cfg.iter_limit = kDefaultIterLimit;
     t->cfg.random_probes = kDefaultRandomProbes;

@@ -205,19 +205,31 @@ def test_iteration_cap_ends_ops_with_a_status(variant):
         p.close()
 
 
-@pytest.mark.parametrize("tpb,bps", [(32, 1), (128, 2), (512, 0), (1024, 1)])
-def test_launch_shapes(tpb, bps):
+@pytest.mark.parametrize("variant,tpb,bps", [("staged", 32, 1), ("staged", 128, 2), ("staged", 256, 0),
+                                             ("staged", 512, 1), ("direct", 32, 1), ("direct", 128, 2),
+                                             ("direct", 512, 0), ("direct", 1024, 1)])
+def test_launch_shapes(variant, tpb, bps):
     w = W.bulk_workload(20000, 0.8, 20000, 0.5, 5000, seed=4)
-    for variant in VARIANTS:
-        p = Pair(w.num_buckets, w.hash_a, w.hash_b, variant=variant, n_hint=20000,
-                 threads_per_block=tpb, blocks_per_sm=bps)
-        try:
-            p.insert(w.keys, w.values)
-            p.search(w.search.keys)
-            p.delete(w.delete_keys)
-            p.check_structure()
-        finally:
-            p.close()
+    p = Pair(w.num_buckets, w.hash_a, w.hash_b, variant=variant, n_hint=20000,
+             threads_per_block=tpb, blocks_per_sm=bps)
+    try:
+        p.insert(w.keys, w.values)
+        p.search(w.search.keys)
+        p.delete(w.delete_keys)
+        p.check_structure()
+    finally:
+        p.close()
+
+
+def test_staged_block_too_large_is_rejected():
+    """32 warps of two 4 KB tile buffers exceed the 227 KB of shared memory a block may use."""
+    t = sh.SlabHash(16, 3, 4, 1024)
+    try:
+        with pytest.raises(sh.SlabError):
+            t.configure(variant=sh.SLAB_VARIANT_STAGED, threads_per_block=1024)
+        t.configure(variant=sh.SLAB_VARIANT_DIRECT, threads_per_block=1024)
+    finally:
+        t.close()
 
 
 def test_side_stream():
