@@ -15,8 +15,9 @@
 // memory and the source lane then acts on it: it reads the value (search),
 // writes the tombstone (delete) or issues the 64-bit CAS of the pair (replace).
 // All source lanes act in the same instructions, so the 32 CASes of a tile are in
-// flight together and their results are checked once. Ops that must follow a
-// next pointer, or whose CAS lost a race, restage just their slabs and go round
+// flight together and their results are checked once. A claim that lost its race
+// tries the following pair of the same slab at once; ops that must follow a next
+// pointer, or that ran off their slab, restage just their slabs and go round
 // again; a full list grows through SlabAlloc exactly as in the paper.
 #pragma once
 #include "slab_device.cuh"
@@ -152,7 +153,10 @@ __global__ void staged_kernel(TableView T, BatchArgs A) {
                 const uint32_t mm = __ballot_sync(kFull, pred);
                 if (lane == 0) ballots[s] = mm;
             };
-            if (first) {
+            if (first && pend == kFull) {  // the common case: no per-op branch, steps overlap
+#pragma unroll
+                for (uint32_t s = 0; s < 32; ++s) step(s, buf[s * 32u + off[s & 7u]]);
+            } else if (first) {
 #pragma unroll
                 for (uint32_t s = 0; s < 32; ++s)
                     if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
@@ -167,16 +171,18 @@ __global__ void staged_kernel(TableView T, BatchArgs A) {
             // the source lanes act on their ballots (Sec. 4.3)
             const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
             uint32_t* gslab = T.slabs + (uint64_t)u * kWordsPerSlab;
+            const uint32_t myop = kKind == kKindMixed ? co : fixed_op<kKind>();
             bool cas_wait = false, cas_new = false, need_slab = false;
             unsigned long long cas_exp = 0, cas_got = 0;
+            uint32_t d = 0;
             if (pending) {
                 if (m) {
-                    const uint32_t d = (uint32_t)(__ffs(m) - 1);
-                    if (co == kOpSearch) {
+                    d = (uint32_t)(__ffs(m) - 1);
+                    if (myop == kOpSearch) {
                         res = kKeyOnly ? 0u : buf[swz(lane, d + 1u)];
                         fnd = 1u;
                         pending = false;
-                    } else if (co == kOpDelete) {
+                    } else if (myop == kOpDelete) {
                         st_relaxed(gslab + d, kTombstone);
                         res = 1u;
                         fnd = 1u;
@@ -203,7 +209,7 @@ __global__ void staged_kernel(TableView T, BatchArgs A) {
                 } else {
                     const uint32_t nx = buf[swz(lane, kAddressLane)];
                     if (nx == kEmptyKey) {
-                        if (co == kOpInsert) need_slab = true;
+                        if (myop == kOpInsert) need_slab = true;
                         else pending = false;  // end of the list: not found
                     } else if (valid_next(T, nx)) {
                         cur = nx;
@@ -213,10 +219,32 @@ __global__ void staged_kernel(TableView T, BatchArgs A) {
                     }
                 }
             }
-            if (cas_wait && cas_got == cas_exp) {  // otherwise: restage this slab and retry
-                fnd = cas_new ? 0u : 1u;
-                res = cas_new ? 1u : 0u;
-                pending = false;
+            // A claim of an empty pair that lost its race learns from the CAS which key
+            // took the pair. If that key is another one, the pair after it is the next
+            // empty candidate: slots fill in (slab, lane) order and are never emptied
+            // on this path, so every earlier pair of the slab holds a different key and
+            // a successful CAS there keeps keys unique. Claims that meet their own key
+            // (a replace race) or run off the slab restage and go round again.
+            constexpr uint32_t kPairStride = kKeyOnly ? 1u : 2u;
+            constexpr uint32_t kLastKeyLane = kKeyOnly ? 29u : 28u;
+            if constexpr (kKind == kKindInsert || kKind == kKindMixed) {
+                while (cas_wait) {
+                    if (cas_got == cas_exp) {
+                        fnd = cas_new ? 0u : 1u;
+                        res = cas_new ? 1u : 0u;
+                        pending = false;
+                        break;
+                    }
+                    if (!cas_new || (uint32_t)cas_got == ck || d + kPairStride > kLastKeyLane) break;
+                    d += kPairStride;
+                    if constexpr (kKeyOnly) {
+                        cas_got = atomicCAS(gslab + d, kEmptyKey, ck);
+                    } else {
+                        cas_exp = pack_pair(kEmptyKey, kEmptyKey);
+                        cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
+                                            pack_pair(ck, cv));
+                    }
+                }
             }
             // full lists grow by one slab each (warp-wide SlabAlloc, Sec. 5)
             for (uint32_t q = __ballot_sync(kFull, need_slab); q; q &= q - 1u) {
