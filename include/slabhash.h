@@ -228,6 +228,31 @@ int slab_free_batch(slab_table *t, const uint32_t *d_addrs, uint32_t n, void *st
  * equal 32 * num_memory_blocks. */
 int slab_copy_bitmaps(const slab_table *t, uint32_t *d_dst, uint64_t n_words, void *stream);
 
+/*
+ * Slab-list length histogram and chain totals, with no device allocation at all.
+ * The paper has no counterpart: this is a library service for callers that
+ * cannot call cudaMalloc at the moment they need table statistics - a thread in
+ * the middle of CUDA stream capture (an allocation there is illegal or breaks
+ * the capture), a serving loop whose device memory is fully reserved by another
+ * allocator (a fresh cudaMalloc would fail or fragment that pool), or a
+ * latency-critical path that cannot afford the device synchronization an
+ * allocation may cause. It walks every list like slab_stats and counts buckets
+ * by slab count: h_hist[i] (n_bins uint64, host) = buckets whose list has i + 1
+ * slabs, the last bin taking every longer list. h_totals (nullable, 6 uint64,
+ * host) = the slab_stats totals. 1 <= n_bins <= 1024; a larger n_bins, or a
+ * current device other than the table's, returns SLAB_ERR_INVALID_ARG.
+ * Scratch: a fixed device array of 1032 uint64 (about 8 KiB) compiled into the
+ * library; every GPU that loads the library holds it until the process exits.
+ * The first call on a device resolves the array's device address (once per
+ * device, with that device current), so make the first call on each device
+ * before any stream capture. The array is shared by all calls and keeps the last
+ * call's counts: each call clears it on `stream` first, and calls that overlap
+ * on the GPU (other streams, other host threads) race on it. Synchronizes
+ * `stream`. Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+int slab_chain_histogram_noalloc(slab_table *t, uint32_t n_bins, uint64_t *h_hist, uint64_t *h_totals,
+                                 void *stream);
+
 /* Human-readable name of a return code. Never NULL. */
 const char *slab_error_string(int rc);
 

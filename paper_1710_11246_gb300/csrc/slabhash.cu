@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <mutex>
 #include <new>
 
 #include "../../include/slabhash.h"
@@ -502,3 +503,118 @@ int slab_copy_bitmaps(const slab_table* t, uint32_t* d_dst, uint64_t n_words, vo
 }
 
 }  // extern "C"
+
+// ======================================================= no-allocation variant
+// A variant of the chain-statistics kernel for callers that must not allocate
+// device memory: its counters live in a file-scope device array instead of the
+// table's own counter block. See slab_chain_histogram_noalloc in slabhash.h.
+namespace {
+
+constexpr uint32_t kNoAllocTotals = 8;      // the six slab_stats totals, padded
+constexpr uint32_t kNoAllocMaxBins = 1024;  // largest histogram the array can hold
+constexpr int kNoAllocMaxDevices = 64;
+
+// 8 KiB + 64 B on every device that loads the library, held until exit.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocTotals + kNoAllocMaxBins];
+
+std::mutex g_noalloc_mutex;
+unsigned long long* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `dev`, resolved once per device with
+// that device current. The host-side name of the array is only a stand-in and
+// must never be passed to a kernel.
+unsigned long long* noalloc_scratch(int dev) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        g_noalloc_ptr[dev] = static_cast<unsigned long long*>(p);
+    }
+    return g_noalloc_ptr[dev];
+}
+
+// stats_kernel's walk, binning each list's slab count (last bin: that many or
+// more) in a block-shared histogram that is added to the scratch at the end.
+template <bool kKeyOnly>
+__global__ void chain_histogram_kernel(TableView T, uint32_t n_bins, unsigned long long* acc) {
+    extern __shared__ unsigned int hist[];
+    constexpr uint32_t kMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    constexpr uint32_t kPerSlab = kKeyOnly ? 30u : 15u;
+    for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint32_t lane = lane_id();
+    const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long live_sum = 0, used_sum = 0, slab_sum = 0, bad = 0, linked = 0;
+    for (uint32_t b = warp_gid; b < T.num_buckets; b += nwarps) {
+        uint32_t cur = kEmptyKey, used = 0, live = 0, n = 0;
+        bool prefix_ok = true, prev_full = true;
+        for (uint64_t guard = 0; guard <= (uint64_t)T.num_blocks * kUnitsPerBlock; ++guard) {
+            const uint32_t w = ld_coherent(slab_ptr(T, b, cur) + lane);
+            const uint32_t u = __ballot_sync(kFull, w != kEmptyKey) & kMask;
+            const uint32_t l = __ballot_sync(kFull, w != kEmptyKey && w != kTombstone) & kMask;
+            const uint32_t cnt = __popc(u);
+            uint32_t want = 0, m = kMask;
+            for (uint32_t i = 0; i < cnt; ++i) { want |= m & (0u - m); m &= m - 1u; }
+            if (u != want || !prev_full) prefix_ok = false;
+            prev_full = cnt == kPerSlab;
+            used += cnt;
+            live += __popc(l);
+            ++n;
+            const uint32_t nx = __shfl_sync(kFull, w, kAddressLane);
+            if (nx == kEmptyKey) break;
+            if (!valid_next(T, nx)) {
+                prefix_ok = false;
+                break;
+            }
+            cur = nx;
+        }
+        if (lane == 0) atomicAdd(&hist[min(n, n_bins) - 1u], 1u);
+        live_sum += live; used_sum += used; slab_sum += n; linked += n - 1; bad += prefix_ok ? 0 : 1;
+    }
+    if (lane == 0) {
+        atomicAdd(acc + 0, live_sum);
+        atomicAdd(acc + 1, used_sum);
+        atomicAdd(acc + 2, slab_sum);
+        atomicAdd(acc + 4, bad);
+        atomicAdd(acc + 5, linked);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x)
+        if (hist[i]) atomicAdd(acc + kNoAllocTotals + i, (unsigned long long)hist[i]);
+}
+
+}  // namespace
+
+extern "C" int slab_chain_histogram_noalloc(slab_table* t, uint32_t n_bins, uint64_t* h_hist, uint64_t* h_totals,
+                                            void* stream) {
+    if (!t || !h_hist || n_bins == 0 || n_bins > kNoAllocMaxBins) return SLAB_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SLAB_ERR_CUDA;
+    if (dev != t->device || dev < 0 || dev >= kNoAllocMaxDevices) return SLAB_ERR_INVALID_ARG;
+    unsigned long long* acc = noalloc_scratch(dev);
+    if (!acc) return SLAB_ERR_CUDA;
+    // every call starts from zeroed counters; the array keeps the previous call's values
+    if (cudaMemsetAsync(acc, 0, (kNoAllocTotals + n_bins) * sizeof(unsigned long long), S(stream)) != cudaSuccess)
+        return SLAB_ERR_CUDA;
+    const TableView T = view(t);
+    const uint32_t grid = util_grid(t, (uint64_t)t->num_buckets * 32, 256);
+    const size_t smem = n_bins * sizeof(unsigned int);
+    if (t->mode == SLAB_MODE_KEY_ONLY)
+        chain_histogram_kernel<true><<<grid, 256, smem, S(stream)>>>(T, n_bins, acc);
+    else
+        chain_histogram_kernel<false><<<grid, 256, smem, S(stream)>>>(T, n_bins, acc);
+    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    const uint64_t words = (uint64_t)t->num_blocks * 32;
+    popcount_kernel<<<util_grid(t, words, 256), 256, 0, S(stream)>>>(t->d_bitmaps, words, acc);
+    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    unsigned long long tot[kNoAllocTotals];
+    if (cudaMemcpyAsync(h_hist, acc + kNoAllocTotals, n_bins * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                        S(stream)) != cudaSuccess ||
+        cudaMemcpyAsync(tot, acc, sizeof(tot), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess ||
+        cudaStreamSynchronize(S(stream)) != cudaSuccess)
+        return SLAB_ERR_CUDA;
+    if (h_totals)
+        for (int i = 0; i < 6; ++i) h_totals[i] = tot[i];
+    return SLAB_OK;
+}

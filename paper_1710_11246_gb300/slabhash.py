@@ -30,6 +30,7 @@ EXPORTED = [
     "slab_insert_batch", "slab_delete_batch", "slab_search_batch", "slab_mixed_batch", "slab_status",
     "slab_stats", "slab_export", "slab_bucket_of", "slab_alloc_batch", "slab_free_batch",
     "slab_copy_bitmaps", "slab_error_string", "slab_probe_random_lines", "slab_probe_random_cas",
+    "slab_chain_histogram_noalloc",
 ]
 
 
@@ -88,6 +89,7 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_error_string": (C.c_char_p, [i32]),
             "slab_probe_random_lines": (i32, [vp, u64, u64, u32, i32, i32, vp, vp]),
             "slab_probe_random_cas": (i32, [vp, u64, u64, u32, i32, i32, vp]),
+            "slab_chain_histogram_noalloc": (i32, [vp, u32, C.POINTER(u64), C.POINTER(u64), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -256,6 +258,20 @@ def slab_probe_random_cas(buf, footprint_lines: int, n_ops: int, seed: int, ops_
     _check(load_library().slab_probe_random_cas(
         _dptr(buf, 8, footprint_lines * 16, "buf"), footprint_lines, n_ops, seed, ops_in_flight,
         threads_per_block, _stream(stream)), "slab_probe_random_cas")
+
+
+def slab_chain_histogram_noalloc(t: int, n_bins: int, stream=None):
+    """(histogram of slabs per list as a uint64 numpy array, slab_stats-style totals).
+
+    The library allocates no device memory for this call; see slabhash.h."""
+    import numpy as np
+    hist = np.zeros(int(n_bins), dtype=np.uint64)
+    tot = (C.c_uint64 * 6)()
+    _check(load_library().slab_chain_histogram_noalloc(
+        t, int(n_bins), hist.ctypes.data_as(C.POINTER(C.c_uint64)), tot, _stream(stream)),
+        "slab_chain_histogram_noalloc")
+    return hist, dict(live=tot[0], slots=tot[1], slabs=tot[2], pool_allocated=tot[3], prefix_violations=tot[4],
+                      linked=tot[5])
 
 
 # ------------------------------------------------------------------ convenience
