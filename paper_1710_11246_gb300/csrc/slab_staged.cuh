@@ -25,9 +25,22 @@
 
 namespace slab {
 
-constexpr uint32_t kTileWords = 32u * kWordsPerSlab;             // one slab per lane: 4 KB
-constexpr uint32_t kStagedWordsPerWarp = 2u * kTileWords + 32u;  // two tile buffers + 32 ballot words
+constexpr uint32_t kTileWords = 32u * kWordsPerSlab;  // one slab per lane: 4 KB
 constexpr uint32_t kNoOpCode = 0xFFu;
+
+// Kernels whose ops claim pairs with a CAS stage each tile's slabs just before
+// serving it (a stale snapshot would make claims lose races to other warps); the
+// next tile's base slabs are only pulled into L2 ahead of time. Read-only and
+// tombstone-only kernels stage a whole tile ahead into a second buffer.
+template <int kKind>
+constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
+// per warp: one or two tile buffers + 32 ballot words
+template <int kKind>
+constexpr uint32_t kStagedWordsPerWarp = (kClaims<kKind> ? 1u : 2u) * kTileWords + 32u;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 __device__ __forceinline__ void cp_async_16(uint32_t smem_addr, const void* gptr) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr), "l"(gptr) : "memory");
@@ -67,8 +80,9 @@ __global__ void staged_kernel(TableView T, BatchArgs A) {
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
     constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
     const uint32_t lane = lane_id();
-    uint32_t* wsm = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp;
-    uint32_t* ballots = wsm + 2u * kTileWords;
+    constexpr bool kJit = kClaims<kKind>;
+    uint32_t* wsm = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp<kKind>;
+    uint32_t* ballots = wsm + (kJit ? 1u : 2u) * kTileWords;
     const uint32_t wsm_s = (uint32_t)__cvta_generic_to_shared(wsm);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -97,32 +111,46 @@ __global__ void staged_kernel(TableView T, BatchArgs A) {
     };
     auto walks = [](uint32_t k, uint32_t o) { return o <= kOpSearch && k < kTombstone; };
 
-    // prologue: tile t staged into buffer 0, tile t + nwarps loading
+    // prologue: tile t staged into buffer 0 (or pulled into L2), tile t + nwarps loading
     uint32_t ck, cv, co;
     fetch(t, ck, cv, co);
     uint32_t cb = walks(ck, co) ? bucket_of(T, ck) : 0u;
-    stage_slabs(T, wsm_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
-    cp_async_commit();
+    if constexpr (kJit) {
+        if (walks(ck, co)) prefetch_l2(T.slabs + (uint64_t)cb * kWordsPerSlab);
+    } else {
+        stage_slabs(T, wsm_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
+        cp_async_commit();
+    }
     uint32_t nk, nv, no;
     fetch(t + nwarps, nk, nv, no);
     uint32_t parity = 0;
 
     for (; t < ntiles; t += nwarps) {
-        // (1) next tile: hash its keys and start staging its base slabs
+        // (1) next tile: hash its keys and start moving its base slabs closer
         const bool nwalk = walks(nk, no);
         const uint32_t nb = nwalk ? bucket_of(T, nk) : 0u;
-        stage_slabs(T, wsm_s + (parity ^ 1u) * kTileWords * 4u, nb, __ballot_sync(kFull, nwalk), lane);
-        cp_async_commit();
+        if constexpr (kJit) {
+            if (nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kWordsPerSlab);
+        } else {
+            stage_slabs(T, wsm_s + (parity ^ 1u) * kTileWords * 4u, nb, __ballot_sync(kFull, nwalk), lane);
+            cp_async_commit();
+        }
         // (2) the tile after it: start its loads
         uint32_t mk, mv, mo;
         fetch(t + 2u * nwarps, mk, mv, mo);
-        // (3) this tile's base slabs were committed one tile ago
-        cp_async_wait<1>();
+        // (3) this tile's base slabs: committed one tile ago, or staged now
+        if constexpr (kJit) {
+            stage_slabs(T, wsm_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
+            cp_async_commit();
+            cp_async_wait<0>();
+        } else {
+            cp_async_wait<1>();
+        }
         __syncwarp();
 
         // (4) serve this tile
-        const uint32_t* buf = wsm + parity * kTileWords;
-        const uint32_t buf_s = wsm_s + parity * kTileWords * 4u;
+        const uint32_t* buf = wsm + (kJit ? 0u : parity) * kTileWords;
+        const uint32_t buf_s = wsm_s + (kJit ? 0u : parity) * kTileWords * 4u;
         const uint32_t idx = t * 32u + lane;
         bool pending = walks(ck, co);
         if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
