@@ -322,6 +322,130 @@ def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24):
     return best
 
 
+# ---------------------------------------------------------------- sweep
+def _time_ms(fn, stream, flush):
+    import torch
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def sweep(args, device):
+    """Extra JSON lines: the bulk benchmark over beta and hit rate (Sec. 6.1), the
+    SlabAlloc microbenchmark (Sec. 5) and full-size concurrent batches (Sec. 6.3)."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    sh.load_library()
+    dev = sh.as_device_u32
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    reps = 5
+
+    def best(fn):
+        return min(_time_ms(fn, stream, flush) for _ in range(reps))
+
+    # bulk: build, search at 0/50/100 % hit, delete, for every beta
+    for beta in W.CONFIG2_BETAS:
+        w = W.config2(beta, 0.5, args.seed)
+        stream_k = W.KeyStream(args.seed)
+        stream_k.take(N_KEYS + N_SEARCH)
+        rng = np.random.default_rng([args.seed, 0x5EA])
+        absent = stream_k.take(N_SEARCH)
+        hit100 = w.keys[rng.permutation(N_KEYS)]
+        queries = {0.0: absent, 0.5: w.search.keys, 1.0: hit100}
+        t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 21)
+        h = t.handle
+        kb, vb, kd = dev(w.keys), dev(w.values), dev(w.delete_keys)
+        out = torch.empty(N_SEARCH, dtype=torch.int32, device=device)
+        fnd = torch.empty(N_SEARCH, dtype=torch.uint8, device=device)
+
+        def build():
+            sh.slab_reset(h, stream)
+            sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+        ms_build = best(build)  # includes the reset fill
+        with torch.cuda.stream(stream):
+            sh.slab_reset(h, stream)
+            sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+        torch.cuda.synchronize()
+        tot = t.stats()
+        util = 8.0 * tot["live"] / (128.0 * tot["slabs"])
+        rates = {}
+        for hr, q in queries.items():
+            dq = dev(q)
+            ms = best(lambda: sh.slab_search_batch(h, dq, out, fnd, stream=stream))
+            rates[f"search_{int(hr * 100)}"] = round(N_SEARCH / (ms * 1e3), 1)
+        snap = None
+        ms_del = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                sh.slab_reset(h, stream)
+                sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+            ms_del.append(_time_ms(lambda: sh.slab_delete_batch(h, kd, None, stream=stream), stream, flush))
+        rc, flags = t.status(stream)
+        line = {"sweep": "bulk", "beta": beta, "num_buckets": w.num_buckets, "unit": "Mops/s",
+                "build_incl_reset": round(N_KEYS / (ms_build * 1e3), 1), **rates,
+                "delete": round(N_DELETE / (min(ms_del) * 1e3), 1), "utilization": round(util, 4),
+                "slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4), "status": rc}
+        print(json.dumps(line), flush=True)
+        t.close()
+        del snap
+
+    # SlabAlloc: 2^24 single-slab allocations (one per lane), then 2^24 frees
+    n = 1 << 24
+    t = sh.SlabHash(8, 3, 4, 1 << 25)
+    addrs = torch.empty(n, dtype=torch.int32, device=device)
+    a_ms, f_ms = [], []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            sh.slab_reset(t.handle, stream)
+        a_ms.append(_time_ms(lambda: sh.slab_alloc_batch(t.handle, addrs, stream=stream), stream, flush))
+        f_ms.append(_time_ms(lambda: sh.slab_free_batch(t.handle, addrs, stream=stream), stream, flush))
+    rc, flags = t.status(stream)
+    bm_zero = bool((t.bitmaps() == 0).all().item())
+    print(json.dumps({"sweep": "slaballoc", "allocations": n, "pool_slabs": 1 << 25, "unit": "Mops/s",
+                      "alloc": round(n / (min(a_ms) * 1e3), 1), "free": round(n / (min(f_ms) * 1e3), 1),
+                      "status": rc, "bitmaps_clear_after_free": bm_zero}), flush=True)
+    t.close()
+    del addrs
+
+    # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
+    for ratios in W.CONFIG3_RATIOS:
+        w = W.config2(BETA, HIT, args.seed)
+        ks = W.KeyStream(args.seed)
+        ks.take(N_KEYS + N_SEARCH)
+        rng = np.random.default_rng([args.seed, 0xC0C0])
+        live = w.keys
+        batches = []
+        for _ in range(64):
+            mb, live = W.mixed_batch(ks, live, N_MIXED, ratios, rng)
+            batches.append((torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)))
+        t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 22)
+        h = t.handle
+        res = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+        with torch.cuda.stream(stream):
+            sh.slab_insert_batch(h, dev(w.keys), dev(w.values), None, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        for ops, keys, vals in batches:
+            ms.append(_time_ms(lambda: sh.slab_mixed_batch(h, ops, keys, vals, res, None, stream=stream),
+                               stream, flush))
+        rc, flags = t.status(stream)
+        tot = t.stats()
+        print(json.dumps({"sweep": "mixed", "ratios": ratios, "batches": 64, "batch_ops": N_MIXED,
+                          "unit": "Mops/s", "mean": round(64 * N_MIXED / (sum(ms) * 1e3), 1),
+                          "first_batch": round(N_MIXED / (ms[0] * 1e3), 1),
+                          "last_batch": round(N_MIXED / (ms[-1] * 1e3), 1),
+                          "final_slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4),
+                          "status": rc}), flush=True)
+        t.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,6 +458,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="print the beta / hit-rate, SlabAlloc and concurrent-batch lines instead")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -346,6 +472,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    if args.sweep:
+        return sweep(args, device)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=device)
 

@@ -74,8 +74,14 @@ __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, 
     }
 }
 
+// Register cap of the staged kernels: more resident warps hide more of each
+// tile's read and CAS latency.
+#ifndef SLAB_STAGED_MAXNREG
+#define SLAB_STAGED_MAXNREG 80
+#endif
+
 template <int kKind, bool kKeyOnly>
-__global__ void staged_kernel(TableView T, BatchArgs A) {
+__global__ void __maxnreg__(SLAB_STAGED_MAXNREG) staged_kernel(TableView T, BatchArgs A) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
     constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
