@@ -39,6 +39,23 @@ POOL_SLABS = 1 << 20
 OPS_PER_STEP = N_KEYS + N_SEARCH + N_DELETE + N_MIXED
 PHASES = ("reset", "build", "search", "delete", "mixed")
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each staged
+# kernel from one ncu capture of this workload (profiles/staged_kernels_bench_step_beta0.6_ncu.md).
+# They describe the kernel sources they were taken from and are dropped as soon as
+# those sources change.
+KERNEL_SOURCES = ("slab_device.cuh", "slab_wcws.cuh", "slab_staged.cuh", "slabhash.cu")
+NCU_TRAFFIC = {"sources_sha256": "88744b4d2df8458e",
+               "build": 103.61e6, "search": 99.29e6, "delete": 60.83e6, "mixed": 66.78e6}
+
+
+def ncu_traffic(phase: str):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1710_11246_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return NCU_TRAFFIC.get(phase) if h.hexdigest()[:16] == NCU_TRAFFIC["sources_sha256"] else None
+
 
 def make_step_inputs(seed: int = 0):
     """The step's batches (deterministic for a seed)."""
@@ -505,8 +522,10 @@ def main():
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
         achieved = alg[dom] / (mean[dom] * 1e-3) / 1e9
+        traffic = ncu_traffic(dom) if args.variant == "staged" else None
         roof = {"bound": "hbm", "kernel": f"{dom} ({args.variant}_kernel)", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "algorithmic_bytes": alg[dom],
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "lines_per_op": {p: round(lines[p] / ops[p], 4) for p in ops}}
         if not args.no_probe:
