@@ -70,18 +70,23 @@ __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, 
         const uint32_t s = 4u * j + (lane >> 3);
         const uint32_t us = __shfl_sync(kFull, u, s);
         if ((mask >> s) & 1u)
-            cp_async_16(stage + (s * 32u + ((c ^ (s & 7u)) << 2)) * 4u, T.slabs + (uint64_t)us * kWordsPerSlab + c * 4u);
+            cp_async_16(stage + (s * 32u + ((c ^ (s & 7u)) << 2)) * 4u,
+                                T.slabs + (uint64_t)us * kWordsPerSlab + c * 4u);
     }
 }
 
-// Register cap of the staged kernels: more resident warps hide more of each
-// tile's read and CAS latency.
+// Register caps of the staged kernels: more resident warps hide more of each
+// tile's read latency (all kernels) and claim round trip (insert, mixed).
 #ifndef SLAB_STAGED_MAXNREG
 #define SLAB_STAGED_MAXNREG 80
 #endif
+#ifndef SLAB_CLAIM_MAXNREG
+#define SLAB_CLAIM_MAXNREG 56
+#endif
 
 template <int kKind, bool kKeyOnly>
-__global__ void __maxnreg__(SLAB_STAGED_MAXNREG) staged_kernel(TableView T, BatchArgs A) {
+__global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MAXNREG)
+    staged_kernel(TableView T, BatchArgs A) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
     constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
@@ -160,6 +165,7 @@ __global__ void __maxnreg__(SLAB_STAGED_MAXNREG) staged_kernel(TableView T, Batc
         const uint32_t idx = t * 32u + lane;
         bool pending = walks(ck, co);
         if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
+
         uint32_t res = default_result(co), fnd = 0, cur = kEmptyKey, rounds = 0;
         bool first = true;
         for (;;) {
