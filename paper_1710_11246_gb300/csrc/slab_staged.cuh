@@ -34,9 +34,10 @@ constexpr uint32_t kNoOpCode = 0xFFu;
 // tombstone-only kernels stage a whole tile ahead into a second buffer.
 template <int kKind>
 constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
-// per warp: one or two tile buffers + 32 ballot words
+// per warp: one or two tile buffers, then 32 ballot words, the tile's 32 keys and
+// its 32 op codes (bytes)
 template <int kKind>
-constexpr uint32_t kStagedWordsPerWarp = (kClaims<kKind> ? 1u : 2u) * kTileWords + 32u;
+constexpr uint32_t kStagedWordsPerWarp = (kClaims<kKind> ? 1u : 2u) * kTileWords + 32u + 32u + 8u;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -94,6 +95,8 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
     constexpr bool kJit = kClaims<kKind>;
     uint32_t* wsm = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp<kKind>;
     uint32_t* ballots = wsm + (kJit ? 1u : 2u) * kTileWords;
+    uint32_t* skeys = ballots + 32;
+    uint8_t* sops = reinterpret_cast<uint8_t*>(skeys + 32);
     const uint32_t wsm_s = (uint32_t)__cvta_generic_to_shared(wsm);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -157,6 +160,8 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
         } else {
             cp_async_wait<1>();
         }
+        skeys[lane] = ck;  // the WCWS steps read keys four at a time from here
+        if constexpr (kKind == kKindMixed) sops[lane] = (uint8_t)co;
         __syncwarp();
 
         // (4) serve this tile
@@ -178,24 +183,37 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
                 cp_async_wait<0>();
                 __syncwarp();
             }
-            // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10)
-            auto step = [&](uint32_t s, uint32_t data) {
-                const uint32_t skey = __shfl_sync(kFull, ck, s);
+            // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
+            // The source key is broadcast from the shared copy of the tile's keys.
+            auto match = [&](uint32_t data, uint32_t skey, uint32_t sop) {
                 bool pred;
                 if constexpr (kKind == kKindInsert) {
                     pred = data == skey || data == kEmptyKey;
                 } else if constexpr (kKind == kKindMixed) {
-                    const uint32_t sop = __shfl_sync(kFull, co, s);
                     pred = data == skey || (sop == kOpInsert && data == kEmptyKey);
                 } else {
                     pred = data == skey;
                 }
-                const uint32_t mm = __ballot_sync(kFull, pred);
+                return __ballot_sync(kFull, pred);
+            };
+            auto step = [&](uint32_t s, uint32_t data) {
+                const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? sops[s] : 0u);
                 if (lane == 0) ballots[s] = mm;
             };
-            if (first && pend == kFull) {  // the common case: no per-op branch, steps overlap
+            if (first && pend == kFull) {
+                // the common case: four ops per key load and per ballot store, no branches
 #pragma unroll
-                for (uint32_t s = 0; s < 32; ++s) step(s, buf[s * 32u + off[s & 7u]]);
+                for (uint32_t g = 0; g < 8; ++g) {
+                    const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
+                    const uint32_t o4 = kKind == kKindMixed ? reinterpret_cast<const uint32_t*>(sops)[g] : 0u;
+                    const uint32_t s0 = 4u * g;
+                    uint4 b4;
+                    b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, o4 & 0xFFu);
+                    b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, (o4 >> 8) & 0xFFu);
+                    b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, (o4 >> 16) & 0xFFu);
+                    b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, o4 >> 24);
+                    if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
+                }
             } else if (first) {
 #pragma unroll
                 for (uint32_t s = 0; s < 32; ++s)
