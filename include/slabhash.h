@@ -115,7 +115,9 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
 void slab_destroy(slab_table *t);
 
 /* Empty the table: every slot and next pointer EMPTY, every SlabAlloc bitmap
- * bit clear, status word zero. One fill kernel on `stream`. */
+ * bit clear, status word zero. One kernel on `stream` that refills the base
+ * slabs and only the pool slabs the bitmaps mark as allocated: free pool slabs
+ * always hold only EMPTY words (so slab_free_batch requires empty slabs). */
 int slab_reset(slab_table *t, void *stream);
 
 /* Geometry of the table. */

@@ -88,6 +88,31 @@ __global__ void fill_kernel(uint4* slabs, uint64_t n16, uint4* bitmaps, uint64_t
     if (tid == 0) misc[0] = 0;
 }
 
+// Reset of a table in use: refill the base slabs with EMPTY and, through the
+// bitmaps, exactly the pool slabs that are allocated, then clear the bitmaps.
+// Pool slabs that are free always hold only EMPTY words: they are filled at
+// create, written only after being allocated and linked, and a slab that lost its
+// link race is freed unwritten.
+__global__ void reset_kernel(uint4* base, uint64_t base16, uint4* pool, uint32_t* bitmaps, uint64_t words,
+                             uint32_t* misc) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4 ones = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
+    for (uint64_t i = tid; i < base16; i += stride) base[i] = ones;
+    for (uint64_t w = tid; w < words; w += stride) {
+        uint32_t bits = bitmaps[w];
+        if (!bits) continue;
+        bitmaps[w] = 0;
+        const uint64_t first_unit = (w >> 5) * kUnitsPerBlock + (w & 31u) * 32u;
+        for (; bits; bits &= bits - 1u) {
+            uint4* slab = pool + (first_unit + (uint64_t)(__ffs(bits) - 1)) * 8u;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) slab[c] = ones;
+        }
+    }
+    if (tid == 0) misc[0] = 0;
+}
+
 // One warp per bucket: walk the list, count used and live key lanes and slabs,
 // and check that used slots form a prefix in (slab, lane) order.
 template <bool kKeyOnly>
@@ -258,6 +283,15 @@ uint32_t util_grid(const slab_table* t, uint64_t work, int tpb) {
     return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)t->sm_count * 8));
 }
 
+// Every slab EMPTY, every bitmap word zero: the state of a new table.
+int fill_table(slab_table* t, void* stream) {
+    const uint64_t n16 = ((uint64_t)t->num_buckets + t->pool_slabs) * 8;  // uint4 per 16 bytes
+    const uint64_t b16 = (uint64_t)t->num_blocks * 8;
+    fill_kernel<<<util_grid(t, n16, 256), 256, 0, S(stream)>>>(
+        reinterpret_cast<uint4*>(t->d_slabs), n16, reinterpret_cast<uint4*>(t->d_bitmaps), b16, t->d_misc);
+    return launch_rc();
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -322,7 +356,7 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     t->cfg.blocks_per_sm = 0;
     t->cfg.iter_limit = kDefaultIterLimit;
     t->cfg.random_probes = kDefaultRandomProbes;
-    if (cudaMemset(t->d_misc, 0, 128) != cudaSuccess || slab_reset(t, nullptr) != SLAB_OK ||
+    if (cudaMemset(t->d_misc, 0, 128) != cudaSuccess || fill_table(t, nullptr) != SLAB_OK ||
         cudaDeviceSynchronize() != cudaSuccess) {
         slab_destroy(t);
         return SLAB_ERR_CUDA;
@@ -342,10 +376,12 @@ void slab_destroy(slab_table* t) {
 
 int slab_reset(slab_table* t, void* stream) {
     if (!t) return SLAB_ERR_INVALID_ARG;
-    const uint64_t n16 = ((uint64_t)t->num_buckets + t->pool_slabs) * 8;  // uint4 per 16 bytes
-    const uint64_t b16 = (uint64_t)t->num_blocks * 8;
-    fill_kernel<<<util_grid(t, n16, 256), 256, 0, S(stream)>>>(
-        reinterpret_cast<uint4*>(t->d_slabs), n16, reinterpret_cast<uint4*>(t->d_bitmaps), b16, t->d_misc);
+    const uint64_t base16 = (uint64_t)t->num_buckets * 8;
+    const uint64_t words = (uint64_t)t->num_blocks * 32;
+    reset_kernel<<<util_grid(t, std::max(base16, words), 256), 256, 0, S(stream)>>>(
+        reinterpret_cast<uint4*>(t->d_slabs), base16,
+        reinterpret_cast<uint4*>(t->d_slabs + (uint64_t)t->num_buckets * kWordsPerSlab), t->d_bitmaps, words,
+        t->d_misc);
     return launch_rc();
 }
 

@@ -232,6 +232,33 @@ def test_staged_block_too_large_is_rejected():
         t.close()
 
 
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_reset_after_use_empties_the_table(variant):
+    """slab_reset refills the base slabs and the allocated pool slabs only; a table
+    reset after long chains and stray allocations behaves like a new one."""
+    from oracle import OracleTable
+    keys = W.KeyStream(21).take(3000)
+    a, b = W.hash_params(21)
+    p = Pair(2, a, b, variant=variant, n_hint=3000)
+    try:
+        p.insert(keys, W.values_for(keys))
+        p.delete(keys[::7])
+        stray = torch.empty(100, dtype=torch.int32, device="cuda")
+        sh.slab_alloc_batch(p.g.handle, stray)
+        p.g.reset()
+        tot = p.g.stats()
+        assert tot["live"] == 0 and tot["slots"] == 0 and tot["slabs"] == 2
+        assert tot["pool_allocated"] == 0 and tot["linked"] == 0
+        assert (host(p.g.bitmaps()) == 0).all()
+        p.o.close()
+        p.o = OracleTable(2, a, b)
+        p.insert(keys[::2], W.values_for(keys[::2]))
+        p.search(keys)
+        p.check_structure()
+    finally:
+        p.close()
+
+
 def test_side_stream():
     w = W.bulk_workload(30000, 0.6, 30000, 0.5, 3000, seed=8)
     s = torch.cuda.Stream()
