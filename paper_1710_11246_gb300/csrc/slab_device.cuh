@@ -38,6 +38,7 @@ struct TableView {
     uint32_t iter_limit;
     uint32_t random_probes;
     uint32_t epoch;       // distinct per launch; spreads resident blocks over launches
+    uint32_t prefetch_l2; // claim kernels pull the next tile's base slabs into L2 (tables larger than L2)
 };
 
 struct BatchArgs {

@@ -30,7 +30,9 @@ constexpr uint32_t kNoOpCode = 0xFFu;
 
 // Kernels whose ops claim pairs with a CAS stage each tile's slabs just before
 // serving it (a stale snapshot would make claims lose races to other warps); the
-// next tile's base slabs are only pulled into L2 ahead of time. Read-only and
+// next tile's base slabs are only pulled into L2 ahead of time, and only when the
+// base slabs do not fit comfortably in L2 (otherwise the extra L2 requests cost
+// more than they save). Read-only and
 // tombstone-only kernels stage a whole tile ahead into a second buffer.
 template <int kKind>
 constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
@@ -130,7 +132,7 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
     fetch(t, ck, cv, co);
     uint32_t cb = walks(ck, co) ? bucket_of(T, ck) : 0u;
     if constexpr (kJit) {
-        if (walks(ck, co)) prefetch_l2(T.slabs + (uint64_t)cb * kWordsPerSlab);
+        if (T.prefetch_l2 && walks(ck, co)) prefetch_l2(T.slabs + (uint64_t)cb * kWordsPerSlab);
     } else {
         stage_slabs(T, wsm_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
         cp_async_commit();
@@ -144,7 +146,7 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
         const bool nwalk = walks(nk, no);
         const uint32_t nb = nwalk ? bucket_of(T, nk) : 0u;
         if constexpr (kJit) {
-            if (nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kWordsPerSlab);
+            if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kWordsPerSlab);
         } else {
             stage_slabs(T, wsm_s + (parity ^ 1u) * kTileWords * 4u, nb, __ballot_sync(kFull, nwalk), lane);
             cp_async_commit();

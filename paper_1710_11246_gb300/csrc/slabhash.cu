@@ -30,6 +30,7 @@ struct slab_table {
     uint32_t* d_misc = nullptr;       // [0] status word, [2..] 8 x u64 counters
     uint64_t device_bytes = 0;
     int max_smem_optin = 0;
+    int l2_bytes = 0;
     slab_config cfg{};
     uint32_t epoch = 0;
 };
@@ -58,6 +59,7 @@ TableView view(slab_table* t) {
     v.iter_limit = t->cfg.iter_limit;
     v.random_probes = t->cfg.random_probes;
     v.epoch = ++t->epoch;
+    v.prefetch_l2 = (uint64_t)t->num_buckets * 128ull > (uint64_t)t->l2_bytes / 2;
     return v;
 }
 
@@ -328,7 +330,8 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     if (cudaGetDevice(&t->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&t->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&t->l2_bytes, cudaDevAttrL2CacheSize, t->device) != cudaSuccess) {
         delete t;
         return SLAB_ERR_CUDA;
     }
