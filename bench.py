@@ -431,6 +431,34 @@ def sweep(args, device):
     t.close()
     del addrs
 
+    # learned bucket function vs universal hash on clustered keys (2^22, beta = 0.6)
+    w = W.config4(seed=args.seed)
+    kb, vb, kq = dev(w.keys), dev(w.values), dev(w.search.keys)
+    out = torch.empty(N_SEARCH, dtype=torch.int32, device=device)
+    fnd = torch.empty(N_SEARCH, dtype=torch.uint8, device=device)
+    line = {"sweep": "learned", "keys": len(w.keys), "clusters": 64, "num_buckets": w.num_buckets,
+            "sample_stride": 100, "unit": "Mops/s"}
+    for label, policy in (("universal", sh.SLAB_LEARN_MEASURE), ("learned", sh.SLAB_LEARN_ALWAYS)):
+        t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 21)
+        h = t.handle
+        fit_ms = _time_ms(lambda: sh.slab_learn_buckets(h, kb, 100, policy, stream=stream), stream, flush)
+        rep = sh.slab_learn_buckets(h, kb, 100, policy, stream=stream)
+        with torch.cuda.stream(stream):
+            sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+        torch.cuda.synchronize()
+        _, slabs, tot = t.stats(per_bucket=True)
+        hist = np.bincount(np.minimum(sh.to_host_u32(slabs), 16)).tolist()
+        ms = min(_time_ms(lambda: sh.slab_search_batch(h, kq, out, fnd, stream=stream), stream, flush)
+                 for _ in range(5))
+        rc, _ = t.status(stream)
+        line[label] = {"search_50": round(N_SEARCH / (ms * 1e3), 1), "fit_ms": round(fit_ms, 3),
+                       "mean_slabs": round(tot["slabs"] / w.num_buckets, 4), "max_slabs": int(max(
+                           np.flatnonzero(np.bincount(sh.to_host_u32(slabs))))),
+                       "slabs_histogram_1_to_16plus": hist[1:], "status": rc}
+        line["report"] = rep
+        t.close()
+    print(json.dumps(line), flush=True)
+
     # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
     for ratios in W.CONFIG3_RATIOS:
         w = W.config2(BETA, HIT, args.seed)

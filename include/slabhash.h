@@ -204,7 +204,48 @@ int slab_stats(slab_table *t, uint32_t *d_slots, uint32_t *d_slabs, uint64_t *h_
 int slab_export(slab_table *t, uint32_t *d_buckets, uint32_t *d_keys, uint32_t *d_values,
                 uint64_t capacity, uint64_t *h_count, void *stream);
 
-/* h(k) for n keys (Sec. 3.3), as the batch kernels compute it. d_buckets_out: n uint32. */
+/*
+ * Learned bucket function (a library extension; the paper hashes with the
+ * universal hash of Sec. 3.3). A two-level piecewise-linear model of the key
+ * set's CDF in FP32: a root line maps a key to one of 1024 leaves, the leaf's line
+ * maps it to a bucket; each line is evaluated as fl(fl(a * x) + b) with x the key
+ * rounded to float, floored and clamped. Model: 2 + 2 * 1024 floats (root a, b,
+ * then a, b per leaf).
+ *
+ * slab_learn_buckets fits the model on the sample keys[0], keys[s], keys[2s], ...
+ * (s = sample_stride; at most 2^20 sample keys): the sample is sorted; the root
+ * fits leaf position i * 1024 / m against the i-th smallest of the m sample keys
+ * by least squares, and each leaf fits bucket position i * B / m over the sample
+ * keys the root sends to it (a leaf with none is flat where they would start).
+ * Least-squares moments are exact integer sums over the targets scaled by m;
+ * each line is a = (n Sxy - Sx Sy) / (n Sxx - Sx^2) / m,
+ * b = ((Sy - a m Sx) / n) / m in correctly rounded double, then rounded to float
+ * (flat at the mean when all x are equal). It
+ * then counts, for all n keys, the slabs per bucket each function would give
+ * (max(1, ceil(load / M))) and reports mean and maximum for both. Policy:
+ * SLAB_LEARN_AUTO uses the model only if neither its mean nor its maximum is
+ * worse than the universal hash's; SLAB_LEARN_ALWAYS uses it; SLAB_LEARN_MEASURE
+ * keeps the universal hash. The table must hold no keys (call it after create or
+ * slab_reset, before inserting): SLAB_ERR_INVALID_ARG otherwise. Uses
+ * stream-ordered device scratch (sample + one counter per bucket) and
+ * synchronizes `stream`.
+ */
+enum slab_learn_policy { SLAB_LEARN_AUTO = 0, SLAB_LEARN_ALWAYS = 1, SLAB_LEARN_MEASURE = 2 };
+typedef struct slab_learn_report {
+    uint32_t sample_size;          /* m */
+    uint32_t use_learned;          /* bucket function now in use: 1 the model, 0 the universal hash */
+    uint32_t max_slabs_learned, max_slabs_universal;
+    double mean_slabs_learned, mean_slabs_universal;
+} slab_learn_report;
+int slab_learn_buckets(slab_table *t, const uint32_t *d_keys, uint32_t n, uint32_t sample_stride, int policy,
+                       slab_learn_report *out, void *stream);
+
+/* Copy the fitted model (2 + 2 * 1024 floats) to h_model; *h_in_use (nullable)
+ * receives 1 if the table's buckets come from it. */
+int slab_get_model(const slab_table *t, float *h_model, uint32_t *h_in_use);
+
+/* The bucket of each of n keys as the batch kernels compute it: h(k) (Sec. 3.3),
+ * or the learned model when the table uses it. d_buckets_out: n uint32. */
 int slab_bucket_of(slab_table *t, const uint32_t *d_keys, uint32_t *d_buckets_out, uint32_t n,
                    void *stream);
 

@@ -26,7 +26,7 @@ def build_oracle(force: bool = False) -> str:
     """Compile slab_oracle.c with the host C compiler (portable flags only)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -58,6 +58,15 @@ def load_oracle(path: str | None = None):
             lib.oracle_utilization.argtypes = [C.c_void_p]
             lib.oracle_export.restype = C.c_uint64
             lib.oracle_export.argtypes = [C.c_void_p, u32p, u32p, u32p, C.c_uint64]
+            f32p = C.POINTER(C.c_float)
+            lib.oracle_learned_bucket.restype = C.c_uint32
+            lib.oracle_learned_bucket.argtypes = [f32p, C.c_uint32, C.c_uint32]
+            lib.oracle_use_model.restype = C.c_int
+            lib.oracle_use_model.argtypes = [C.c_void_p, f32p]
+            lib.oracle_fit_points.argtypes = [u32p, u32p, C.c_uint64, f32p]
+            lib.oracle_learn_model.restype = C.c_uint64
+            lib.oracle_learn_model.argtypes = [u32p, C.c_uint64, C.c_uint32, C.c_uint32, f32p]
+            lib.oracle_chain_profile.argtypes = [C.c_void_p, u32p, C.c_uint64, u64p, u32p]
             lib.oracle_check_alloc.restype = C.c_int
             lib.oracle_check_alloc.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, C.c_uint32, u64p]
             if path is not None:
@@ -152,6 +161,19 @@ class OracleTable:
         return slots, slabs, dict(live=int(tot[0]), slots=int(tot[1]), slabs=int(tot[2]),
                                   reserved=int(tot[3]))
 
+    def use_model(self, model):
+        """Switch an empty table to a learned bucket function (2 + 2048 float32)."""
+        model = np.ascontiguousarray(model, dtype=np.float32)
+        if self.lib.oracle_use_model(self.h, _ptr(model, C.c_float)) != 0:
+            raise ValueError("the table is not empty")
+
+    def chain_profile(self, keys):
+        """(sum, max) of slabs per bucket the keys would form under this table's buckets."""
+        keys = _u32(keys)
+        sm, mx = C.c_uint64(0), C.c_uint32(0)
+        self.lib.oracle_chain_profile(self.h, _ptr(keys, C.c_uint32), len(keys), C.byref(sm), C.byref(mx))
+        return int(sm.value), int(mx.value)
+
     def utilization(self) -> float:
         return float(self.lib.oracle_utilization(self.h))
 
@@ -170,6 +192,36 @@ def hash_of(a: int, b: int, num_buckets: int, key: int, lib=None) -> int:
     """h(k; a, b) = ((a k + b) mod p) mod B for one key, no table needed."""
     lib = lib if lib is not None else load_oracle()
     return int(lib.oracle_hash(int(a), int(b), int(num_buckets), int(key)))
+
+
+MODEL_FLOATS = 2 + 2 * 1024
+
+
+def learn_model(keys, stride: int, num_buckets: int, lib=None):
+    """Fit the two-level learned bucket model on keys[::stride]; returns (model, m)."""
+    lib = lib if lib is not None else load_oracle()
+    keys = _u32(keys)
+    model = np.zeros(MODEL_FLOATS, np.float32)
+    m = lib.oracle_learn_model(_ptr(keys, C.c_uint32), len(keys), int(stride), int(num_buckets),
+                               _ptr(model, C.c_float))
+    return model, int(m)
+
+
+def learned_buckets(model, num_buckets: int, keys, lib=None) -> np.ndarray:
+    lib = lib if lib is not None else load_oracle()
+    model = np.ascontiguousarray(model, dtype=np.float32)
+    mp = _ptr(model, C.c_float)
+    return np.array([lib.oracle_learned_bucket(mp, int(num_buckets), int(k)) for k in np.asarray(keys)],
+                    dtype=np.uint32)
+
+
+def fit_points(xs, ys, lib=None):
+    """(a, b) of the least-squares line through integer points, as the model fits it."""
+    lib = lib if lib is not None else load_oracle()
+    xs, ys = _u32(xs), _u32(ys)
+    ab = np.zeros(2, np.float32)
+    lib.oracle_fit_points(_ptr(xs, C.c_uint32), _ptr(ys, C.c_uint32), len(xs), _ptr(ab, C.c_float))
+    return ab
 
 
 def check_alloc(addrs, bitmaps, num_blocks: int, blocks_per_super: int = 1 << 14, lib=None):

@@ -49,6 +49,8 @@ typedef struct {
 
 typedef struct {
     uint32_t B;        /* number of buckets (base slabs) */
+    int learned;       /* buckets from the learned model instead of the universal hash */
+    float model[2 + 2 * 1024];
     uint32_t M;        /* data elements per slab: 15 (key-value) or 30 (key only) */
     int key_only;
     uint64_t a, b, p;  /* universal hash parameters */
@@ -90,9 +92,175 @@ uint32_t oracle_hash(uint32_t a, uint32_t b, uint32_t num_buckets, uint32_t key)
     return (uint32_t)((x % OR_PRIME) % num_buckets);
 }
 
+/*
+ * Learned bucket function (a library extension, not in the paper). A model is
+ * 2 + 2 * 1024 floats: a root line (a, b) picks one of 1024 leaves, the leaf's
+ * line (a, b) gives the bucket. Each line is evaluated in float as a * x, rounded,
+ * plus b, rounded (this file is compiled with -ffp-contract=off so the two
+ * roundings stay separate), with x the key rounded to float; the result is floored
+ * and clamped to [0, limit), NaN and negatives giving 0.
+ */
+static uint32_t linear_piece(float a, float b, float x, uint32_t limit)
+{
+    float p = a * x;
+    p = p + b;
+    if (!(p >= 0.0f)) return 0;
+    if (p >= (float)limit) return limit - 1;
+    return (uint32_t)p;
+}
+
+uint32_t oracle_learned_bucket(const float *model, uint32_t num_buckets, uint32_t key)
+{
+    float x = (float)key;
+    uint32_t leaf = linear_piece(model[0], model[1], x, 1024);
+    return linear_piece(model[2 + 2 * leaf], model[3 + 2 * leaf], x, num_buckets);
+}
+
 uint32_t oracle_bucket(const or_table *t, uint32_t key)
 {
+    if (t->learned) return oracle_learned_bucket(t->model, t->B, key);
     return oracle_hash((uint32_t)t->a, (uint32_t)t->b, t->B, key);
+}
+
+/* Replace the table's bucket function by a learned model (the table must be empty). */
+int oracle_use_model(or_table *t, const float *model)
+{
+    if (t->live != 0) return -1;
+    for (uint32_t i = 0; i < t->B; i++)
+        if (t->bk[i].len) return -1;
+    memcpy(t->model, model, sizeof(t->model));
+    t->learned = 1;
+    return 0;
+}
+
+typedef unsigned __int128 or_u128;
+typedef __int128 or_s128;
+
+static double u128_to_double(or_u128 v)
+{
+    double hi = (double)(uint64_t)(v >> 64);
+    double lo = (double)(uint64_t)v;
+    hi = hi * 18446744073709551616.0; /* 2^64: exact */
+    return hi + lo;
+}
+
+static double s128_to_double(or_s128 v)
+{
+    if (v < 0) return -u128_to_double((or_u128)(-v));
+    return u128_to_double((or_u128)v);
+}
+
+/* Least squares line y = (a' x + b') / q through n >= 1 points (x, q y) with exact
+ * integer moments of x and of the scaled targets q y: a' = (n Sxy - Sx Sy) /
+ * (n Sxx - Sx^2), b' = (Sy - a' Sx) / n, a = a' / q, b = b' / q, each operation in
+ * correctly rounded double, then rounded to float; a' = 0, b' = Sy / n when the
+ * points share one x. */
+static void fit_line(uint64_t n, or_u128 sx, or_u128 sy, or_u128 sxx, or_u128 sxy, uint64_t q, float *a, float *b)
+{
+    or_s128 N = (or_s128)n;
+    or_s128 den = N * (or_s128)sxx - (or_s128)sx * (or_s128)sx;
+    or_s128 num = N * (or_s128)sxy - (or_s128)sx * (or_s128)sy;
+    double dn = (double)n, dq = (double)q;
+    double a1 = 0.0, b1;
+    if (den > 0) {
+        a1 = s128_to_double(num) / s128_to_double(den);
+        double t = a1 * u128_to_double(sx);
+        double u = u128_to_double(sy) - t;
+        b1 = u / dn;
+    } else {
+        b1 = u128_to_double(sy) / dn;
+    }
+    double a64 = a1 / dq;
+    double b64 = b1 / dq;
+    *a = (float)a64;
+    *b = (float)b64;
+}
+
+static void add_point(or_u128 *sx, or_u128 *sy, or_u128 *sxx, or_u128 *sxy, uint32_t x, uint64_t y)
+{
+    *sx += x;
+    *sy += y;
+    *sxx += (or_u128)((uint64_t)x * x);
+    *sxy += (or_u128)x * (or_u128)y;
+}
+
+/* The least-squares line through the integer points (xs[i], ys[i]), i < n (n >= 1). */
+void oracle_fit_points(const uint32_t *xs, const uint32_t *ys, uint64_t n, float *ab)
+{
+    or_u128 sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (uint64_t i = 0; i < n; i++) add_point(&sx, &sy, &sxx, &sxy, xs[i], ys[i]);
+    fit_line(n, sx, sy, sxx, sxy, 1, &ab[0], &ab[1]);
+}
+
+static int cmp_u32(const void *p, const void *q)
+{
+    uint32_t x = *(const uint32_t *)p, y = *(const uint32_t *)q;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Fit the two-level model on the sample keys[0], keys[stride], keys[2 stride], ...:
+ * sort the m sample keys; the root fits leaf position i * 1024 / m against the i-th
+ * smallest key; each leaf fits bucket position i * B / m over the sample keys the
+ * root sends to it; a leaf with no sample key is flat at c * B / m, c the number of
+ * sample keys the root sends to lower leaves. Returns m, or 0 if n or stride is 0.
+ */
+uint64_t oracle_learn_model(const uint32_t *keys, uint64_t n, uint32_t stride, uint32_t num_buckets, float *model)
+{
+    if (n == 0 || stride == 0) return 0;
+    uint64_t m = (n + stride - 1) / stride;
+    uint32_t *x = (uint32_t *)malloc(m * sizeof(uint32_t));
+    uint32_t *leaf = (uint32_t *)malloc(m * sizeof(uint32_t));
+    if (!x || !leaf) abort();
+    for (uint64_t i = 0; i < m; i++) x[i] = keys[i * stride];
+    qsort(x, m, sizeof(uint32_t), cmp_u32);
+
+    or_u128 sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (uint64_t i = 0; i < m; i++) add_point(&sx, &sy, &sxx, &sxy, x[i], i * 1024);
+    fit_line(m, sx, sy, sxx, sxy, m, &model[0], &model[1]);
+    for (uint64_t i = 0; i < m; i++) leaf[i] = linear_piece(model[0], model[1], (float)x[i], 1024);
+
+    uint64_t below = 0; /* sample keys sent to leaves < j */
+    for (uint32_t j = 0; j < 1024; j++) {
+        or_u128 lx = 0, ly = 0, lxx = 0, lxy = 0;
+        uint64_t cnt = 0;
+        for (uint64_t i = 0; i < m; i++) {
+            if (leaf[i] != j) continue;
+            add_point(&lx, &ly, &lxx, &lxy, x[i], i * (uint64_t)num_buckets);
+            cnt++;
+        }
+        if (cnt) {
+            fit_line(cnt, lx, ly, lxx, lxy, m, &model[2 + 2 * j], &model[3 + 2 * j]);
+        } else {
+            double start = (double)(below * (uint64_t)num_buckets) / (double)m;
+            model[2 + 2 * j] = 0.0f;
+            model[3 + 2 * j] = (float)start;
+        }
+        below += cnt;
+    }
+    free(x);
+    free(leaf);
+    return m;
+}
+
+/* Slabs per bucket that `n` keys would form under the table's bucket function:
+ * *sum and *max of max(1, ceil(load / M)) over the buckets. */
+void oracle_chain_profile(const or_table *t, const uint32_t *keys, uint64_t n, uint64_t *sum, uint32_t *max)
+{
+    uint32_t *load = (uint32_t *)calloc(t->B, sizeof(uint32_t));
+    if (!load) abort();
+    for (uint64_t i = 0; i < n; i++)
+        if (keys[i] < OR_KEY_LIMIT) load[oracle_bucket(t, keys[i])]++;
+    uint64_t s = 0;
+    uint32_t mx = 0;
+    for (uint32_t b = 0; b < t->B; b++) {
+        uint32_t k = load[b] == 0 ? 1 : (load[b] + t->M - 1) / t->M;
+        s += k;
+        if (k > mx) mx = k;
+    }
+    free(load);
+    *sum = s;
+    *max = mx;
 }
 
 /* Position of the live slot holding `key` in bucket `bk`, or -1. */

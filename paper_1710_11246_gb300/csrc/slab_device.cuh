@@ -27,6 +27,7 @@ enum : int { kKindSearch = 0, kKindInsert = 1, kKindDelete = 2, kKindMixed = 3 }
 
 struct TableView {
     uint32_t* slabs;      // B base slabs, then the SlabAlloc pool
+    const float* model;   // learned bucket function (root a, b; 1024 leaves a, b)
     uint32_t* pool;       // slabs + B * 32: unit `a` of the pool at pool + a * 32
     uint32_t* bitmaps;    // 32 words per memory block
     uint32_t* status;     // device status word (kFlag*)
@@ -39,6 +40,7 @@ struct TableView {
     uint32_t random_probes;
     uint32_t epoch;       // distinct per launch; spreads resident blocks over launches
     uint32_t prefetch_l2; // claim kernels pull the next tile's base slabs into L2 (tables larger than L2)
+    uint32_t learned;     // 1: buckets come from the learned model, 0: from the universal hash
 };
 
 struct BatchArgs {
@@ -57,13 +59,35 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 // and Kurz's direct remainder ("Faster remainder by direct computation", 2019):
 // with m = ceil(2^64 / B), n mod B = floor(((m n) mod 2^64) * B / 2^64) for
 // every 32-bit n and B.
-__device__ __forceinline__ uint32_t bucket_of(const TableView& T, uint32_t k) {
+__device__ __forceinline__ uint32_t universal_bucket(const TableView& T, uint32_t k) {
     uint64_t x = (uint64_t)T.hash_a * k + T.hash_b;
     uint64_t t = (x >> 32) * 5ull + (x & 0xFFFFFFFFull);  // < 6 * 2^32
     t = (t >> 32) * 5ull + (t & 0xFFFFFFFFull);           // < 2^32 + 30
     uint32_t r = (uint32_t)(t >= kPrime ? t - kPrime : t);
     uint64_t low = T.fastmod_m * r;
     return (uint32_t)__umul64hi(low, (uint64_t)T.num_buckets);
+}
+
+// One linear piece of the learned bucket function, evaluated in FP32 with a
+// separately rounded multiply and add (no fused multiply-add), then floored and
+// clamped to [0, limit): p = a * x + b; NaN and negatives give 0.
+__device__ __forceinline__ uint32_t linear_piece(float a, float b, float x, uint32_t limit) {
+    const float p = __fadd_rn(__fmul_rn(a, x), b);
+    if (!(p >= 0.0f)) return 0u;
+    if (p >= __uint2float_rn(limit)) return limit - 1u;
+    return (uint32_t)p;
+}
+
+// Learned bucket function: two-level piecewise-linear CDF of the key set. The root
+// piece picks one of 1024 leaves, the leaf piece maps the key to a bucket.
+__device__ __forceinline__ uint32_t learned_bucket(const float* model, uint32_t num_buckets, uint32_t k) {
+    const float x = __uint2float_rn(k);
+    const uint32_t leaf = linear_piece(__ldg(model), __ldg(model + 1), x, 1024u);
+    return linear_piece(__ldg(model + 2 + 2 * leaf), __ldg(model + 3 + 2 * leaf), x, num_buckets);
+}
+
+__device__ __forceinline__ uint32_t bucket_of(const TableView& T, uint32_t k) {
+    return T.learned ? learned_bucket(T.model, T.num_buckets, k) : universal_bucket(T, k);
 }
 
 // Slab word reads. Mutating kernels read through L2 with relaxed gpu-scope

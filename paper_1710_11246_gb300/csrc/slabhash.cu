@@ -12,63 +12,21 @@
 #include "../../include/slabhash.h"
 #include "slab_device.cuh"
 #include "slab_staged.cuh"
+#include "slab_table.cuh"
 #include "slab_wcws.cuh"
 
 using namespace slab;
-
-struct slab_table {
-    int device = 0;
-    int sm_count = 0;
-    uint32_t num_buckets = 0;
-    int mode = 0;
-    uint32_t hash_a = 0, hash_b = 0;
-    uint64_t fastmod_m = 0;
-    uint64_t pool_slabs = 0;
-    uint32_t num_blocks = 0;
-    uint32_t* d_slabs = nullptr;      // base slabs then pool
-    uint32_t* d_bitmaps = nullptr;
-    uint32_t* d_misc = nullptr;       // [0] status word, [2..] 8 x u64 counters
-    uint64_t device_bytes = 0;
-    int max_smem_optin = 0;
-    int l2_bytes = 0;
-    slab_config cfg{};
-    uint32_t epoch = 0;
-};
 
 namespace {
 
 constexpr uint32_t kDefaultIterLimit = 1u << 22;
 constexpr uint32_t kDefaultRandomProbes = 256;
 
-unsigned long long* counters(const slab_table* t) {
-    return reinterpret_cast<unsigned long long*>(t->d_misc + 2);
-}
-
-TableView view(slab_table* t) {
-    TableView v;
-    v.slabs = t->d_slabs;
-    v.pool = t->d_slabs + (uint64_t)t->num_buckets * kWordsPerSlab;
-    v.bitmaps = t->d_bitmaps;
-    v.status = t->d_misc;
-    v.fastmod_m = t->fastmod_m;
-    v.num_buckets = t->num_buckets;
-    v.hash_a = t->hash_a;
-    v.hash_b = t->hash_b;
-    v.num_blocks = t->num_blocks;
-    v.pool_units = (uint32_t)t->pool_slabs;
-    v.iter_limit = t->cfg.iter_limit;
-    v.random_probes = t->cfg.random_probes;
-    v.epoch = ++t->epoch;
-    v.prefetch_l2 = (uint64_t)t->num_buckets * 128ull > (uint64_t)t->l2_bytes / 2;
-    return v;
-}
-
-inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
-
-int launch_rc() {
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? SLAB_OK : SLAB_ERR_CUDA;
-}
+using slab_host::counters;
+using slab_host::launch_rc;
+using slab_host::S;
+using slab_host::util_grid;
+using slab_host::view;
 
 bool valid_config(const slab_config& c) {
     return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
@@ -280,10 +238,6 @@ int dispatch(slab_table* t, const BatchArgs& a, void* stream) {
                                          : launch_batch<kKind, false>(t, a, stream);
 }
 
-uint32_t util_grid(const slab_table* t, uint64_t work, int tpb) {
-    const uint64_t want = (work + tpb - 1) / tpb;
-    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)t->sm_count * 8));
-}
 
 // Every slab EMPTY, every bitmap word zero: the state of a new table.
 int fill_table(slab_table* t, void* stream) {
@@ -345,21 +299,24 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     const uint64_t slab_bytes = ((uint64_t)num_buckets + pool) * 128ull;
     const uint64_t bitmap_bytes = blocks * 128ull;
     if (cudaMalloc(&t->d_slabs, slab_bytes) != cudaSuccess) { delete t; cudaGetLastError(); return SLAB_ERR_CUDA; }
+    const uint64_t model_bytes = (2 + 2 * 1024) * sizeof(float);
     if (cudaMalloc(&t->d_bitmaps, bitmap_bytes) != cudaSuccess ||
-        cudaMalloc(&t->d_misc, 128) != cudaSuccess) {
+        cudaMalloc(&t->d_misc, 128) != cudaSuccess || cudaMalloc(&t->d_model, model_bytes) != cudaSuccess) {
         cudaFree(t->d_slabs);
         cudaFree(t->d_bitmaps);
+        cudaFree(t->d_misc);
         delete t;
         cudaGetLastError();
         return SLAB_ERR_CUDA;
     }
-    t->device_bytes = slab_bytes + bitmap_bytes + 128;
+    t->device_bytes = slab_bytes + bitmap_bytes + 128 + model_bytes;
     t->cfg.variant = SLAB_VARIANT_STAGED;
     t->cfg.threads_per_block = 128;
     t->cfg.blocks_per_sm = 0;
     t->cfg.iter_limit = kDefaultIterLimit;
     t->cfg.random_probes = kDefaultRandomProbes;
-    if (cudaMemset(t->d_misc, 0, 128) != cudaSuccess || fill_table(t, nullptr) != SLAB_OK ||
+    if (cudaMemset(t->d_misc, 0, 128) != cudaSuccess || cudaMemset(t->d_model, 0, model_bytes) != cudaSuccess ||
+        fill_table(t, nullptr) != SLAB_OK ||
         cudaDeviceSynchronize() != cudaSuccess) {
         slab_destroy(t);
         return SLAB_ERR_CUDA;
@@ -374,11 +331,13 @@ void slab_destroy(slab_table* t) {
     cudaFree(t->d_slabs);
     cudaFree(t->d_bitmaps);
     cudaFree(t->d_misc);
+    cudaFree(t->d_model);
     delete t;
 }
 
 int slab_reset(slab_table* t, void* stream) {
     if (!t) return SLAB_ERR_INVALID_ARG;
+    t->dirty = false;
     const uint64_t base16 = (uint64_t)t->num_buckets * 8;
     const uint64_t words = (uint64_t)t->num_blocks * 32;
     reset_kernel<<<util_grid(t, std::max(base16, words), 256), 256, 0, S(stream)>>>(
@@ -420,6 +379,7 @@ int slab_insert_batch(slab_table* t, const uint32_t* d_keys, const uint32_t* d_v
                       uint32_t n, void* stream) {
     if (!t || (n && !d_keys) || (n && !d_values && t->mode == SLAB_MODE_KEY_VALUE)) return SLAB_ERR_INVALID_ARG;
     BatchArgs a{nullptr, d_keys, d_values, nullptr, d_found, n};
+    if (n) t->dirty = true;
     return dispatch<kKindInsert>(t, a, stream);
 }
 
@@ -442,6 +402,7 @@ int slab_mixed_batch(slab_table* t, const uint8_t* d_ops, const uint32_t* d_keys
         (n && !d_values && t->mode == SLAB_MODE_KEY_VALUE))
         return SLAB_ERR_INVALID_ARG;
     BatchArgs a{d_ops, d_keys, d_values, d_results, d_found, n};
+    if (n) t->dirty = true;
     return dispatch<kKindMixed>(t, a, stream);
 }
 

@@ -30,8 +30,10 @@ EXPORTED = [
     "slab_insert_batch", "slab_delete_batch", "slab_search_batch", "slab_mixed_batch", "slab_status",
     "slab_stats", "slab_export", "slab_bucket_of", "slab_alloc_batch", "slab_free_batch",
     "slab_copy_bitmaps", "slab_error_string", "slab_probe_random_lines", "slab_probe_random_cas",
-    "slab_chain_histogram_noalloc",
+    "slab_chain_histogram_noalloc", "slab_learn_buckets", "slab_get_model",
 ]
+SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
+MODEL_FLOATS = 2 + 2 * 1024
 
 
 class SlabConfig(C.Structure):
@@ -44,6 +46,12 @@ class SlabInfo(C.Structure):
                 ("hash_a", C.c_uint32), ("hash_b", C.c_uint32), ("pool_slabs", C.c_uint64),
                 ("num_memory_blocks", C.c_uint32), ("blocks_per_super", C.c_uint32),
                 ("num_super_blocks", C.c_uint32), ("sm_count", C.c_uint32), ("device_bytes", C.c_uint64)]
+
+
+class SlabLearnReport(C.Structure):
+    _fields_ = [("sample_size", C.c_uint32), ("use_learned", C.c_uint32), ("max_slabs_learned", C.c_uint32),
+                ("max_slabs_universal", C.c_uint32), ("mean_slabs_learned", C.c_double),
+                ("mean_slabs_universal", C.c_double)]
 
 
 class SlabError(RuntimeError):
@@ -90,6 +98,8 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_probe_random_lines": (i32, [vp, u64, u64, u32, i32, i32, vp, vp]),
             "slab_probe_random_cas": (i32, [vp, u64, u64, u32, i32, i32, vp]),
             "slab_chain_histogram_noalloc": (i32, [vp, u32, C.POINTER(u64), C.POINTER(u64), vp]),
+            "slab_learn_buckets": (i32, [vp, vp, u32, u32, i32, C.POINTER(SlabLearnReport), vp]),
+            "slab_get_model": (i32, [vp, C.POINTER(C.c_float), C.POINTER(u32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -258,6 +268,25 @@ def slab_probe_random_cas(buf, footprint_lines: int, n_ops: int, seed: int, ops_
     _check(load_library().slab_probe_random_cas(
         _dptr(buf, 8, footprint_lines * 16, "buf"), footprint_lines, n_ops, seed, ops_in_flight,
         threads_per_block, _stream(stream)), "slab_probe_random_cas")
+
+
+def slab_learn_buckets(t: int, keys, sample_stride: int = 100, policy: int = SLAB_LEARN_AUTO, n: int | None = None,
+                       stream=None) -> dict:
+    n = keys.numel() if n is None else n
+    rep = SlabLearnReport()
+    _check(load_library().slab_learn_buckets(t, _dptr(keys, 4, n, "keys"), n, int(sample_stride), int(policy),
+                                             C.byref(rep), _stream(stream)), "slab_learn_buckets")
+    return {f: getattr(rep, f) for f, _ in rep._fields_}
+
+
+def slab_get_model(t: int):
+    """(model as float32 numpy array of 2 + 2 * 1024, whether the table uses it)."""
+    import numpy as np
+    model = np.zeros(MODEL_FLOATS, np.float32)
+    in_use = C.c_uint32(0)
+    _check(load_library().slab_get_model(t, model.ctypes.data_as(C.POINTER(C.c_float)), C.byref(in_use)),
+           "slab_get_model")
+    return model, bool(in_use.value)
 
 
 def slab_chain_histogram_noalloc(t: int, n_bins: int, stream=None):

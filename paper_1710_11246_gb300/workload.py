@@ -21,6 +21,9 @@ Recipe (Sec. 6.1 and 6.3: uniform random 32-bit keys, no external dataset):
   to both implementations.
 * Search batches mix present keys (a random subset of the stored keys) and
   absent keys (fresh counters) at a stated hit rate, shuffled.
+* Clustered keys (the learned-bucket workload): draws from 64 Gaussian clusters
+  with uniform centres and standard deviations in [2^10, 2^20], rounded, clamped
+  and deduplicated; absent keys come from the same clusters.
 * Mixed batches (Sec. 6.3) draw fresh inserts, deletes of distinct live keys,
   searches of live keys untouched by the batch and searches of absent keys, in
   stated ratios, shuffled so every op kind can land in one warp. Every key
@@ -185,6 +188,45 @@ def config1(seed: int = 0) -> BulkWorkload:
 def config2(beta: float = 0.6, hit_rate: float = 0.5, seed: int = 0) -> BulkWorkload:
     """2^22 pairs, 2^22 searches at the given hit rate, 2^20 deletes."""
     return bulk_workload(1 << 22, beta, 1 << 22, hit_rate, 1 << 20, seed)
+
+
+def _cluster_draws(rng, centres, sigmas, count):
+    c = rng.integers(0, len(centres), count)
+    x = np.rint(centres[c] + sigmas[c] * rng.standard_normal(count))
+    return np.clip(x, 0, KEY_LIMIT - 1).astype(np.uint64).astype(np.uint32)
+
+
+def clustered_keys(n: int, seed: int = 0, clusters: int = 64, sigma_lo: float = 2.0 ** 10,
+                   sigma_hi: float = 2.0 ** 20, extra: int = 0):
+    """n distinct keys from `clusters` Gaussian clusters (centres uniform in
+    [0, 2^32), standard deviations uniform in [sigma_lo, sigma_hi]), rounded,
+    clamped to [0, 2^32 - 3] and deduplicated, in random order; plus `extra`
+    further distinct keys from the same clusters that are not among the n."""
+    rng = np.random.default_rng([int(seed), 0xC1A5])
+    centres = rng.uniform(0.0, 2.0 ** 32, clusters)
+    sigmas = rng.uniform(sigma_lo, sigma_hi, clusters)
+    pool = np.empty(0, np.uint32)
+    need = n + extra
+    while len(pool) < need:
+        pool = np.unique(np.concatenate([pool, _cluster_draws(rng, centres, sigmas, max(1 << 16, need - len(pool)) * 2)]))
+    pick = rng.permutation(len(pool))[:need]
+    keys = pool[pick]
+    return keys[:n].copy(), keys[n:].copy()
+
+
+def config4(seed: int = 0, n: int = 1 << 22, beta: float = 0.6, hit_rate: float = 0.5) -> BulkWorkload:
+    """Clustered keys: n pairs, searches of n keys at the hit rate (absent keys from
+    the same clusters), no deletes."""
+    n_miss = n - int(round(n * hit_rate))
+    keys, absent = clustered_keys(n, seed, extra=n_miss)
+    rng = np.random.default_rng([int(seed), 0xC4])
+    a, b = hash_params(seed)
+    n_hit = n - n_miss
+    q = np.concatenate([keys[rng.choice(n, n_hit, replace=False)], absent])
+    present = np.concatenate([np.ones(n_hit, bool), np.zeros(n_miss, bool)])
+    perm = rng.permutation(n)
+    return BulkWorkload(buckets_for(n, beta), a, b, keys, values_for(keys), SearchBatch(q[perm], present[perm]),
+                        np.empty(0, np.uint32))
 
 
 CONFIG3_RATIOS = ((0.5, 0.5, 0.0), (0.2, 0.2, 0.6), (0.05, 0.05, 0.9))

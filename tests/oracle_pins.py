@@ -14,7 +14,7 @@ import random
 
 import numpy as np
 
-from oracle.oracle import NOT_FOUND, OracleTable, check_alloc, hash_of
+from oracle.oracle import NOT_FOUND, OracleTable, check_alloc, fit_points, hash_of, learn_model, learned_buckets
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 P = 4294967291
@@ -296,6 +296,76 @@ def pin_alloc_check(lib):
     bm2 = bm.copy()
     bm2[0] = 0b111
     assert check_alloc(addrs, bm2, nb, blocks_per_super=2, lib=lib) == (3, 0)
+
+
+# ------------------------------------------------------- learned bucket function
+def pin_learned_fit_lines(lib):
+    """Least-squares lines through integer points with known answers: collinear
+    points give their line exactly; points sharing one x give a flat line at the
+    mean; two points give the line through both."""
+    assert tuple(fit_points([1, 2, 3], [2, 4, 6], lib=lib)) == (2.0, 0.0)
+    assert tuple(fit_points([0, 2], [1, 3], lib=lib)) == (1.0, 1.0)
+    assert tuple(fit_points([5, 5], [1, 3], lib=lib)) == (0.0, 2.0)
+    assert tuple(fit_points([7], [9], lib=lib)) == (0.0, 9.0)
+    assert tuple(fit_points([10, 20, 30, 40], [5, 5, 5, 5], lib=lib)) == (0.0, 5.0)
+    a, b = fit_points([0, 1 << 31], [0, 1 << 20], lib=lib)
+    assert a == np.float32(2.0 ** -11) and b == 0.0
+
+
+def pin_learned_tiny_golden(lib):
+    """Hand-derived fit and evaluation on four keys (tests/golden/learned_tiny.txt)."""
+    rows = list(_rows("learned_tiny.txt"))
+    keys = np.array([int(v) for v in rows[0][1:]], np.uint32)
+    model, m = learn_model(keys, 1, 8, lib=lib)
+    assert m == 4
+    for row in rows[1:]:
+        if row[0] == "root":
+            assert (model[0], model[1]) == (float(row[1]), float(row[2])), model[:2]
+        elif row[0] == "leaf":
+            j = int(row[1])
+            assert (model[2 + 2 * j], model[3 + 2 * j]) == (float(row[2]), float(row[3])), (j, model[2 + 2 * j:4 + 2 * j])
+        elif row[0] == "bucket":
+            assert int(learned_buckets(model, 8, [int(row[1])], lib=lib)[0]) == int(row[2]), row
+
+
+def pin_learned_uniform_keys_balance(lib):
+    """Evenly spaced keys have a linear CDF, so a model fitted on all of them (in any
+    order) spreads them almost perfectly: every bucket receives n / B keys, give or
+    take two."""
+    n, B = 1 << 16, 4096
+    keys = (np.arange(n, dtype=np.uint64) * 65521 + 12345).astype(np.uint32)
+    model, _ = learn_model(keys[np.random.default_rng(1).permutation(n)], 1, B, lib=lib)
+    load = np.bincount(learned_buckets(model, B, keys, lib=lib), minlength=B)
+    assert load.min() >= n // B - 2 and load.max() <= n // B + 2, (load.min(), load.max())
+
+
+def pin_learned_table_semantics(lib):
+    """Set semantics do not depend on the bucket function: a table on a learned model
+    agrees with the flat-set model, and chain_profile (sum and max of slabs per
+    bucket the keys would form) matches the slabs after inserting those keys."""
+    rng = np.random.default_rng(9)
+    keys = np.unique(rng.integers(0, 1 << 32, 6000, dtype=np.uint64) % 0xFFFFFFFE).astype(np.uint32)
+    B = 300
+    model, _ = learn_model(keys, 3, B, lib=lib)
+    t = OracleTable(B, 11, 13, lib=lib)
+    t.use_model(model)
+    sm, mx = t.chain_profile(keys)
+    f = t.insert(keys, keys ^ np.uint32(77))
+    assert f.sum() == 0
+    _, slabs, tot = t.stats()
+    assert tot["slabs"] == sm and int(slabs.max()) == mx
+    for k, bk in zip(keys[:200].tolist(), t.buckets(keys[:200]).tolist()):
+        assert bk == learned_buckets(model, B, [k], lib=lib)[0]
+    v, found = t.search(keys)
+    assert found.all() and (v == (keys ^ np.uint32(77))).all()
+    ref = FlatSet()
+    for k in keys[:500].tolist():
+        ref.replace(k, k ^ 77)
+    d = t.delete(keys[:100])
+    assert d.all()
+    _, _, tot = t.stats()
+    assert tot["live"] == len(keys) - 100
+    assert int(learned_buckets(model, B, [0, 0xFFFFFFFD], lib=lib).max()) < B
 
 
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -34,6 +34,12 @@ MUTANTS = {
     "utilization_drops_pointer": ("double y = 8.0;", "double y = 0.0;"),
     "bitmap_word_index": ("uint64_t w = block * 32 + unit / 32;", "uint64_t w = block * 32 + unit % 32;"),
     "address_field_width": ("uint32_t blk = (a >> 10) & 0x3FFFu;", "uint32_t blk = (a >> 12) & 0x3FFFu;"),
+    "learned_root_target": ("add_point(&sx, &sy, &sxx, &sxy, x[i], i * 1024);", "add_point(&sx, &sy, &sxx, &sxy, x[i], i * 1000);"),
+    "learned_unsorted_sample": ("qsort(x, m, sizeof(uint32_t), cmp_u32);", "(void)cmp_u32;"),
+    "learned_empty_leaf_start": ("        below += cnt;\n", ""),
+    "learned_intercept_sign": ("double u = u128_to_double(sy) - t;", "double u = u128_to_double(sy) + t;"),
+    "learned_leaf_lookup": ("return linear_piece(model[2 + 2 * leaf], model[3 + 2 * leaf], x, num_buckets);",
+                            "return linear_piece(model[3 + 2 * leaf], model[2 + 2 * leaf], x, num_buckets);"),
 }
 
 
@@ -50,7 +56,8 @@ def test_pins_catch_mutant(name, source, tmp_path):
     src = tmp_path / f"{name}.c"
     src.write_text(source.replace(old, new, 1))
     lib_path = str(tmp_path / f"lib{name}.so")
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", lib_path, str(src)])
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", "-o", lib_path,
+                           str(src)])
     lib = load_oracle(lib_path)
     caught = []
     for pin in ALL_PINS:
