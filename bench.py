@@ -459,6 +459,55 @@ def sweep(args, device):
         t.close()
     print(json.dumps(line), flush=True)
 
+    # 512 independent tables, sizes log-uniform in [2^8, 2^18]: per-table launches vs
+    # one group launch per batch vs the group step replayed from a CUDA graph, and the
+    # autotuned group configuration
+    from paper_1710_11246_gb300 import autotune as AT
+    gw = W.group_workload(512, 1 << 8, 1 << 18, seed=args.seed)
+    ops = 2 * int(gw.sizes.sum())
+    arrays = AT._arrays(gw, device)
+    gout = torch.empty(len(gw.search_keys), dtype=torch.int32, device=device)
+    gfnd = torch.empty(len(gw.search_keys), dtype=torch.uint8, device=device)
+    g = AT.create_group(gw, BETA)
+    line = {"sweep": "group", "tables": 512, "keys": int(gw.sizes.sum()), "ops_per_step": ops,
+            "sizes": "log-uniform [2^8, 2^18]", "unit": "Mops/s"}
+    ms = AT.time_group(g, arrays, gout, gfnd, stream)
+    line["group_launch"] = round(ops / (ms * 1e3), 1)
+    # the same step as 2 x 512 single-table launches through the tables' own handles
+    views = [sh.slab_group_table(g, i) for i in range(512)]
+    st, ks, vs, qs, q = arrays
+    o, so = gw.op_start.tolist(), gw.search_start.tolist()
+
+    def per_table():
+        sh.slab_group_reset(g, stream)
+        for i, t in enumerate(views):
+            if o[i + 1] > o[i]:
+                sh.slab_insert_batch(t, ks[o[i]:o[i + 1]], vs[o[i]:o[i + 1]], None, stream=stream)
+        for i, t in enumerate(views):
+            if so[i + 1] > so[i]:
+                sh.slab_search_batch(t, q[so[i]:so[i + 1]], gout[so[i]:so[i + 1]], gfnd[so[i]:so[i + 1]],
+                                     stream=stream)
+    per_table()
+    torch.cuda.synchronize()
+    ms_pt = min(_time_ms(per_table, stream, flush) for _ in range(3))
+    line["per_table_launches"] = round(ops / (ms_pt * 1e3), 1)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        AT.group_step(g, arrays, gout, gfnd, stream)
+    graph.replay()
+    torch.cuda.synchronize()
+    ms_gr = min(_time_ms(graph.replay, stream, flush) for _ in range(5))
+    line["group_cuda_graph"] = round(ops / (ms_gr * 1e3), 1)
+    rc, _ = sh.slab_group_status(g, stream)
+    line["status"] = rc
+    sh.slab_group_destroy(g)
+    best, cands = AT.tune_group(gw, device=device)
+    line["autotuned"] = {"beta": best.beta, "threads_per_block": best.threads_per_block,
+                         "blocks_per_sm": best.blocks_per_sm, "mops": round(best.mops, 1),
+                         "candidates": len(cands),
+                         "worst_mops": round(min(c.mops for c in cands), 1)}
+    print(json.dumps(line), flush=True)
+
     # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
     for ratios in W.CONFIG3_RATIOS:
         w = W.config2(BETA, HIT, args.seed)

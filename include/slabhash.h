@@ -296,6 +296,45 @@ int slab_copy_bitmaps(const slab_table *t, uint32_t *d_dst, uint64_t n_words, vo
 int slab_chain_histogram_noalloc(slab_table *t, uint32_t n_bins, uint64_t *h_hist, uint64_t *h_totals,
                                  void *stream);
 
+/*
+ * Groups: many independent slab hashes served by one persistent launch (a library
+ * extension; the paper runs one table). The tables' slabs, pools, bitmaps and
+ * status words share one device arena owned by the group; each table keeps its
+ * own B, hash parameters and pool and behaves exactly like a table from
+ * slab_create. A batch for the group is one array of ops sorted by table:
+ * d_op_start (device, ntables + 1 uint32, non-decreasing, d_op_start[0] = 0,
+ * d_op_start[ntables] = total) gives table i the ops
+ * [d_op_start[i], d_op_start[i + 1]); keys, values, results and found are as in
+ * the single-table calls, indexed over the whole batch. One call queues a small
+ * prefix-sum kernel and one persistent launch that serves tiles of 32 ops of one
+ * table each, so the calls can be captured in a CUDA graph.
+ */
+typedef struct slab_group slab_group; /* opaque, library-owned */
+int slab_group_create(uint32_t ntables, const uint32_t *h_num_buckets, const uint32_t *h_hash_a,
+                      const uint32_t *h_hash_b, const uint64_t *h_pool_slabs, int mode, slab_group **out);
+/* Frees the arena and every table handle of the group. */
+void slab_group_destroy(slab_group *g);
+/* A handle to table i of the group, valid until the group is destroyed; every
+ * single-table call accepts it (slab_destroy on it does nothing; the learned
+ * bucket function is not available for tables of a group). */
+int slab_group_table(slab_group *g, uint32_t i, slab_table **out);
+int slab_group_get_config(const slab_group *g, slab_config *out);
+/* threads_per_block, blocks_per_sm, iter_limit and random_probes apply to group launches. */
+int slab_group_set_config(slab_group *g, const slab_config *cfg);
+/* Empty every table of the group (one kernel). */
+int slab_group_reset(slab_group *g, void *stream);
+int slab_group_insert(slab_group *g, const uint32_t *d_op_start, const uint32_t *d_keys, const uint32_t *d_values,
+                      uint8_t *d_found, uint32_t total, void *stream);
+int slab_group_delete(slab_group *g, const uint32_t *d_op_start, const uint32_t *d_keys, uint8_t *d_found,
+                      uint32_t total, void *stream);
+int slab_group_search(slab_group *g, const uint32_t *d_op_start, const uint32_t *d_keys, uint32_t *d_values_out,
+                      uint8_t *d_found, uint32_t total, void *stream);
+int slab_group_mixed(slab_group *g, const uint32_t *d_op_start, const uint8_t *d_ops, const uint32_t *d_keys,
+                     const uint32_t *d_values, uint32_t *d_results, uint8_t *d_found, uint32_t total, void *stream);
+/* Synchronize `stream`, then read and clear every table's status word; *h_flags
+ * (nullable) receives their OR; the return code ranks them as slab_status does. */
+int slab_group_status(slab_group *g, void *stream, uint32_t *h_flags);
+
 /* Human-readable name of a return code. Never NULL. */
 const char *slab_error_string(int rc);
 

@@ -195,6 +195,7 @@ int slab_learn_buckets(slab_table* t, const uint32_t* d_keys, uint32_t n, uint32
     if (!t || !d_keys || n == 0 || sample_stride == 0 || policy < SLAB_LEARN_AUTO || policy > SLAB_LEARN_MEASURE)
         return SLAB_ERR_INVALID_ARG;
     if (t->dirty) return SLAB_ERR_INVALID_ARG;  // keys already stored under the current bucket function
+    if (!t->d_model) return SLAB_ERR_INVALID_ARG;  // tables inside a group have no model storage
     const uint32_t m = (uint32_t)(((uint64_t)n + sample_stride - 1) / sample_stride);
     if (m > kMaxSample) return SLAB_ERR_INVALID_ARG;
     uint32_t p = 2;
@@ -251,7 +252,7 @@ int slab_learn_buckets(slab_table* t, const uint32_t* d_keys, uint32_t n, uint32
 }
 
 int slab_get_model(const slab_table* t, float* h_model, uint32_t* h_in_use) {
-    if (!t || !h_model) return SLAB_ERR_INVALID_ARG;
+    if (!t || !h_model || !t->d_model) return SLAB_ERR_INVALID_ARG;
     if (cudaMemcpy(h_model, t->d_model, (2 + 2 * kLeaves) * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
         return SLAB_ERR_CUDA;
     if (h_in_use) *h_in_use = t->learned ? 1u : 0u;

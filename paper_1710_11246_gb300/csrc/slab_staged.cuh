@@ -78,6 +78,186 @@ __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, 
     }
 }
 
+// Serve one tile of up to 32 ops, one per lane (op index idx, valid where `has`),
+// whose base slabs are staged in slots 0..31 of `buf` (shared byte address
+// buf_s), keys in `skeys` and op codes in `sops`: the WCWS rounds of Fig.
+// "alg:search", each op's source-lane action, restaging for ops that move on,
+// list growth, and the result writes.
+template <int kKind, bool kKeyOnly>
+__device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& A, AllocCtx& ac, uint32_t warp_gid,
+                                           const uint32_t* buf, uint32_t buf_s, uint32_t* ballots,
+                                           const uint32_t* skeys, const uint8_t* sops, const uint32_t (&off)[8],
+                                           uint32_t ck, uint32_t cv, uint32_t co, uint32_t cb, uint32_t idx,
+                                           bool has) {
+    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    const uint32_t lane = lane_id();
+    bool pending = co <= kOpSearch && ck < kTombstone;
+    if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
+
+    uint32_t res = default_result(co), fnd = 0, cur = kEmptyKey, rounds = 0;
+    bool first = true;
+    for (;;) {
+        const uint32_t pend = __ballot_sync(kFull, pending);
+        if (!pend) break;
+        const uint32_t u = cur == kEmptyKey ? cb : T.num_buckets + cur;
+        if (!first) {  // restage only the ops that moved on or must retry
+            stage_slabs(T, buf_s, u, pend, lane);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+        }
+        // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
+        // The source key is broadcast from the shared copy of the tile's keys.
+        auto match = [&](uint32_t data, uint32_t skey, uint32_t sop) {
+            bool pred;
+            if constexpr (kKind == kKindInsert) {
+                pred = data == skey || data == kEmptyKey;
+            } else if constexpr (kKind == kKindMixed) {
+                pred = data == skey || (sop == kOpInsert && data == kEmptyKey);
+            } else {
+                pred = data == skey;
+            }
+            return __ballot_sync(kFull, pred);
+        };
+        auto step = [&](uint32_t s, uint32_t data) {
+            const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? sops[s] : 0u);
+            if (lane == 0) ballots[s] = mm;
+        };
+        if (first && pend == kFull) {
+            // the common case: four ops per key load and per ballot store, no branches
+#pragma unroll
+            for (uint32_t g = 0; g < 8; ++g) {
+                const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
+                const uint32_t o4 = kKind == kKindMixed ? reinterpret_cast<const uint32_t*>(sops)[g] : 0u;
+                const uint32_t s0 = 4u * g;
+                uint4 b4;
+                b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, o4 & 0xFFu);
+                b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, (o4 >> 8) & 0xFFu);
+                b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, (o4 >> 16) & 0xFFu);
+                b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, o4 >> 24);
+                if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
+            }
+        } else if (first) {
+#pragma unroll
+            for (uint32_t s = 0; s < 32; ++s)
+                if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
+        } else {
+            for (uint32_t q = pend; q; q &= q - 1u) {
+                const uint32_t s = (uint32_t)(__ffs(q) - 1);
+                step(s, buf[swz(s, lane)]);
+            }
+        }
+        __syncwarp();
+
+        // the source lanes act on their ballots (Sec. 4.3)
+        const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
+        uint32_t* gslab = T.slabs + (uint64_t)u * kWordsPerSlab;
+        const uint32_t myop = kKind == kKindMixed ? co : fixed_op<kKind>();
+        bool cas_wait = false, cas_new = false, need_slab = false;
+        unsigned long long cas_exp = 0, cas_got = 0;
+        uint32_t d = 0;
+        if (pending) {
+            if (m) {
+                d = (uint32_t)(__ffs(m) - 1);
+                if (myop == kOpSearch) {
+                    res = kKeyOnly ? 0u : buf[swz(lane, d + 1u)];
+                    fnd = 1u;
+                    pending = false;
+                } else if (myop == kOpDelete) {
+                    st_relaxed(gslab + d, kTombstone);
+                    res = 1u;
+                    fnd = 1u;
+                    pending = false;
+                } else if constexpr (kKeyOnly) {
+                    if (buf[swz(lane, d)] == ck) {  // already present
+                        res = 0u;
+                        fnd = 1u;
+                        pending = false;
+                    } else {
+                        cas_exp = kEmptyKey;
+                        cas_got = atomicCAS(gslab + d, kEmptyKey, ck);
+                        cas_wait = true;
+                        cas_new = true;
+                    }
+                } else {
+                    const uint2 pr = *reinterpret_cast<const uint2*>(buf + swz(lane, d));
+                    cas_exp = pack_pair(pr.x, pr.y);
+                    cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
+                                        pack_pair(ck, cv));
+                    cas_wait = true;
+                    cas_new = pr.x == kEmptyKey;
+                }
+            } else {
+                const uint32_t nx = buf[swz(lane, kAddressLane)];
+                if (nx == kEmptyKey) {
+                    if (myop == kOpInsert) need_slab = true;
+                    else pending = false;  // end of the list: not found
+                } else if (valid_next(T, nx)) {
+                    cur = nx;
+                } else {
+                    set_flag(T, kFlagBadPointer);
+                    pending = false;
+                }
+            }
+        }
+        // A claim of an empty pair that lost its race learns from the CAS which key
+        // took the pair. If that key is another one, the pair after it is the next
+        // empty candidate: slots fill in (slab, lane) order and are never emptied
+        // on this path, so every earlier pair of the slab holds a different key and
+        // a successful CAS there keeps keys unique. Claims that meet their own key
+        // (a replace race) or run off the slab restage and go round again.
+        constexpr uint32_t kPairStride = kKeyOnly ? 1u : 2u;
+        constexpr uint32_t kLastKeyLane = kKeyOnly ? 29u : 28u;
+        if constexpr (kKind == kKindInsert || kKind == kKindMixed) {
+            while (cas_wait) {
+                if (cas_got == cas_exp) {
+                    fnd = cas_new ? 0u : 1u;
+                    res = cas_new ? 1u : 0u;
+                    pending = false;
+                    break;
+                }
+                if (!cas_new || (uint32_t)cas_got == ck || d + kPairStride > kLastKeyLane) break;
+                d += kPairStride;
+                if constexpr (kKeyOnly) {
+                    cas_got = atomicCAS(gslab + d, kEmptyKey, ck);
+                } else {
+                    cas_exp = pack_pair(kEmptyKey, kEmptyKey);
+                    cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
+                                        pack_pair(ck, cv));
+                }
+            }
+        }
+        // full lists grow by one slab each (warp-wide SlabAlloc, Sec. 5)
+        for (uint32_t q = __ballot_sync(kFull, need_slab); q; q &= q - 1u) {
+            const int s = __ffs(q) - 1;
+            uint32_t* ps = reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)gslab, s));
+            const uint32_t nx = grow_list(T, ac, warp_gid, ps, s);
+            if ((int)lane == s) {
+                if (nx == kAllocFailed) {
+                    set_flag(T, kFlagOutOfSlabs);
+                    pending = false;
+                } else if (valid_next(T, nx)) {
+                    cur = nx;
+                } else {
+                    set_flag(T, kFlagBadPointer);
+                    pending = false;
+                }
+            }
+        }
+        if (pending && ++rounds >= T.iter_limit) {
+            set_flag(T, kFlagIterLimit);
+            pending = false;
+        }
+        first = false;
+        __syncwarp();
+    }
+    if (has) {
+        if (A.results) A.results[idx] = res;
+        if (A.found) A.found[idx] = (uint8_t)fnd;
+    }
+
+}
+
 // Register caps of the staged kernels: more resident warps hide more of each
 // tile's read latency (all kernels) and claim round trip (insert, mixed).
 #ifndef SLAB_STAGED_MAXNREG
@@ -92,7 +272,6 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
     staged_kernel(TableView T, BatchArgs A) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
-    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
     const uint32_t lane = lane_id();
     constexpr bool kJit = kClaims<kKind>;
     uint32_t* wsm = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp<kKind>;
@@ -170,170 +349,8 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
         const uint32_t* buf = wsm + (kJit ? 0u : parity) * kTileWords;
         const uint32_t buf_s = wsm_s + (kJit ? 0u : parity) * kTileWords * 4u;
         const uint32_t idx = t * 32u + lane;
-        bool pending = walks(ck, co);
-        if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
-
-        uint32_t res = default_result(co), fnd = 0, cur = kEmptyKey, rounds = 0;
-        bool first = true;
-        for (;;) {
-            const uint32_t pend = __ballot_sync(kFull, pending);
-            if (!pend) break;
-            const uint32_t u = cur == kEmptyKey ? cb : T.num_buckets + cur;
-            if (!first) {  // restage only the ops that moved on or must retry
-                stage_slabs(T, buf_s, u, pend, lane);
-                cp_async_commit();
-                cp_async_wait<0>();
-                __syncwarp();
-            }
-            // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
-            // The source key is broadcast from the shared copy of the tile's keys.
-            auto match = [&](uint32_t data, uint32_t skey, uint32_t sop) {
-                bool pred;
-                if constexpr (kKind == kKindInsert) {
-                    pred = data == skey || data == kEmptyKey;
-                } else if constexpr (kKind == kKindMixed) {
-                    pred = data == skey || (sop == kOpInsert && data == kEmptyKey);
-                } else {
-                    pred = data == skey;
-                }
-                return __ballot_sync(kFull, pred);
-            };
-            auto step = [&](uint32_t s, uint32_t data) {
-                const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? sops[s] : 0u);
-                if (lane == 0) ballots[s] = mm;
-            };
-            if (first && pend == kFull) {
-                // the common case: four ops per key load and per ballot store, no branches
-#pragma unroll
-                for (uint32_t g = 0; g < 8; ++g) {
-                    const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
-                    const uint32_t o4 = kKind == kKindMixed ? reinterpret_cast<const uint32_t*>(sops)[g] : 0u;
-                    const uint32_t s0 = 4u * g;
-                    uint4 b4;
-                    b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, o4 & 0xFFu);
-                    b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, (o4 >> 8) & 0xFFu);
-                    b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, (o4 >> 16) & 0xFFu);
-                    b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, o4 >> 24);
-                    if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
-                }
-            } else if (first) {
-#pragma unroll
-                for (uint32_t s = 0; s < 32; ++s)
-                    if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
-            } else {
-                for (uint32_t q = pend; q; q &= q - 1u) {
-                    const uint32_t s = (uint32_t)(__ffs(q) - 1);
-                    step(s, buf[swz(s, lane)]);
-                }
-            }
-            __syncwarp();
-
-            // the source lanes act on their ballots (Sec. 4.3)
-            const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
-            uint32_t* gslab = T.slabs + (uint64_t)u * kWordsPerSlab;
-            const uint32_t myop = kKind == kKindMixed ? co : fixed_op<kKind>();
-            bool cas_wait = false, cas_new = false, need_slab = false;
-            unsigned long long cas_exp = 0, cas_got = 0;
-            uint32_t d = 0;
-            if (pending) {
-                if (m) {
-                    d = (uint32_t)(__ffs(m) - 1);
-                    if (myop == kOpSearch) {
-                        res = kKeyOnly ? 0u : buf[swz(lane, d + 1u)];
-                        fnd = 1u;
-                        pending = false;
-                    } else if (myop == kOpDelete) {
-                        st_relaxed(gslab + d, kTombstone);
-                        res = 1u;
-                        fnd = 1u;
-                        pending = false;
-                    } else if constexpr (kKeyOnly) {
-                        if (buf[swz(lane, d)] == ck) {  // already present
-                            res = 0u;
-                            fnd = 1u;
-                            pending = false;
-                        } else {
-                            cas_exp = kEmptyKey;
-                            cas_got = atomicCAS(gslab + d, kEmptyKey, ck);
-                            cas_wait = true;
-                            cas_new = true;
-                        }
-                    } else {
-                        const uint2 pr = *reinterpret_cast<const uint2*>(buf + swz(lane, d));
-                        cas_exp = pack_pair(pr.x, pr.y);
-                        cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
-                                            pack_pair(ck, cv));
-                        cas_wait = true;
-                        cas_new = pr.x == kEmptyKey;
-                    }
-                } else {
-                    const uint32_t nx = buf[swz(lane, kAddressLane)];
-                    if (nx == kEmptyKey) {
-                        if (myop == kOpInsert) need_slab = true;
-                        else pending = false;  // end of the list: not found
-                    } else if (valid_next(T, nx)) {
-                        cur = nx;
-                    } else {
-                        set_flag(T, kFlagBadPointer);
-                        pending = false;
-                    }
-                }
-            }
-            // A claim of an empty pair that lost its race learns from the CAS which key
-            // took the pair. If that key is another one, the pair after it is the next
-            // empty candidate: slots fill in (slab, lane) order and are never emptied
-            // on this path, so every earlier pair of the slab holds a different key and
-            // a successful CAS there keeps keys unique. Claims that meet their own key
-            // (a replace race) or run off the slab restage and go round again.
-            constexpr uint32_t kPairStride = kKeyOnly ? 1u : 2u;
-            constexpr uint32_t kLastKeyLane = kKeyOnly ? 29u : 28u;
-            if constexpr (kKind == kKindInsert || kKind == kKindMixed) {
-                while (cas_wait) {
-                    if (cas_got == cas_exp) {
-                        fnd = cas_new ? 0u : 1u;
-                        res = cas_new ? 1u : 0u;
-                        pending = false;
-                        break;
-                    }
-                    if (!cas_new || (uint32_t)cas_got == ck || d + kPairStride > kLastKeyLane) break;
-                    d += kPairStride;
-                    if constexpr (kKeyOnly) {
-                        cas_got = atomicCAS(gslab + d, kEmptyKey, ck);
-                    } else {
-                        cas_exp = pack_pair(kEmptyKey, kEmptyKey);
-                        cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
-                                            pack_pair(ck, cv));
-                    }
-                }
-            }
-            // full lists grow by one slab each (warp-wide SlabAlloc, Sec. 5)
-            for (uint32_t q = __ballot_sync(kFull, need_slab); q; q &= q - 1u) {
-                const int s = __ffs(q) - 1;
-                uint32_t* ps = reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)gslab, s));
-                const uint32_t nx = grow_list(T, ac, warp_gid, ps, s);
-                if ((int)lane == s) {
-                    if (nx == kAllocFailed) {
-                        set_flag(T, kFlagOutOfSlabs);
-                        pending = false;
-                    } else if (valid_next(T, nx)) {
-                        cur = nx;
-                    } else {
-                        set_flag(T, kFlagBadPointer);
-                        pending = false;
-                    }
-                }
-            }
-            if (pending && ++rounds >= T.iter_limit) {
-                set_flag(T, kFlagIterLimit);
-                pending = false;
-            }
-            first = false;
-            __syncwarp();
-        }
-        if (idx < A.n) {
-            if (A.results) A.results[idx] = res;
-            if (A.found) A.found[idx] = (uint8_t)fnd;
-        }
+        serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, sops, off, ck, cv, co, cb, idx,
+                                    idx < A.n);
 
         // (5) rotate the pipeline
         ck = nk; cv = nv; co = no; cb = nb;

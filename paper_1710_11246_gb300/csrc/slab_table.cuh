@@ -30,6 +30,7 @@ struct slab_table {
     bool learned = false;             // bucket function in use: learned model or universal hash
     bool model_fitted = false;
     bool dirty = false;               // a batch may have stored keys since create / reset
+    bool owns_memory = true;          // false for a table that lives inside a slab_group's arena
 };
 
 namespace slab_host {

@@ -326,7 +326,7 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
 }
 
 void slab_destroy(slab_table* t) {
-    if (!t) return;
+    if (!t || !t->owns_memory) return;  // tables of a group are freed with the group
     cudaDeviceSynchronize();
     cudaFree(t->d_slabs);
     cudaFree(t->d_bitmaps);

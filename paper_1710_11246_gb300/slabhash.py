@@ -31,6 +31,9 @@ EXPORTED = [
     "slab_stats", "slab_export", "slab_bucket_of", "slab_alloc_batch", "slab_free_batch",
     "slab_copy_bitmaps", "slab_error_string", "slab_probe_random_lines", "slab_probe_random_cas",
     "slab_chain_histogram_noalloc", "slab_learn_buckets", "slab_get_model",
+    "slab_group_create", "slab_group_destroy", "slab_group_table", "slab_group_get_config", "slab_group_set_config",
+    "slab_group_reset", "slab_group_insert", "slab_group_delete", "slab_group_search", "slab_group_mixed",
+    "slab_group_status",
 ]
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
 MODEL_FLOATS = 2 + 2 * 1024
@@ -100,6 +103,17 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_chain_histogram_noalloc": (i32, [vp, u32, C.POINTER(u64), C.POINTER(u64), vp]),
             "slab_learn_buckets": (i32, [vp, vp, u32, u32, i32, C.POINTER(SlabLearnReport), vp]),
             "slab_get_model": (i32, [vp, C.POINTER(C.c_float), C.POINTER(u32)]),
+            "slab_group_create": (i32, [u32, vp, vp, vp, vp, i32, C.POINTER(vp)]),
+            "slab_group_destroy": (None, [vp]),
+            "slab_group_table": (i32, [vp, u32, C.POINTER(vp)]),
+            "slab_group_get_config": (i32, [vp, C.POINTER(SlabConfig)]),
+            "slab_group_set_config": (i32, [vp, C.POINTER(SlabConfig)]),
+            "slab_group_reset": (i32, [vp, vp]),
+            "slab_group_insert": (i32, [vp, vp, vp, vp, vp, u32, vp]),
+            "slab_group_delete": (i32, [vp, vp, vp, vp, u32, vp]),
+            "slab_group_search": (i32, [vp, vp, vp, vp, vp, u32, vp]),
+            "slab_group_mixed": (i32, [vp, vp, vp, vp, vp, vp, vp, u32, vp]),
+            "slab_group_status": (i32, [vp, vp, C.POINTER(u32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -301,6 +315,88 @@ def slab_chain_histogram_noalloc(t: int, n_bins: int, stream=None):
         "slab_chain_histogram_noalloc")
     return hist, dict(live=tot[0], slots=tot[1], slabs=tot[2], pool_allocated=tot[3], prefix_violations=tot[4],
                       linked=tot[5])
+
+
+def slab_group_create(num_buckets, hash_a, hash_b, pool_slabs, mode: int = SLAB_MODE_KEY_VALUE) -> int:
+    import numpy as np
+    nb = np.ascontiguousarray(num_buckets, np.uint32)
+    ha = np.ascontiguousarray(hash_a, np.uint32)
+    hb = np.ascontiguousarray(hash_b, np.uint32)
+    ps = np.ascontiguousarray(pool_slabs, np.uint64)
+    if not (len(nb) == len(ha) == len(hb) == len(ps)):
+        raise ValueError("per-table arrays differ in length")
+    g = C.c_void_p()
+    _check(load_library().slab_group_create(len(nb), nb.ctypes.data, ha.ctypes.data, hb.ctypes.data, ps.ctypes.data,
+                                            mode, C.byref(g)), "slab_group_create")
+    return g.value
+
+
+def slab_group_destroy(g: int) -> None:
+    load_library().slab_group_destroy(g)
+
+
+def slab_group_table(g: int, i: int) -> int:
+    t = C.c_void_p()
+    _check(load_library().slab_group_table(g, int(i), C.byref(t)), "slab_group_table")
+    return t.value
+
+
+def slab_group_get_config(g: int) -> SlabConfig:
+    cfg = SlabConfig()
+    _check(load_library().slab_group_get_config(g, C.byref(cfg)), "slab_group_get_config")
+    return cfg
+
+
+def slab_group_set_config(g: int, cfg: SlabConfig) -> None:
+    _check(load_library().slab_group_set_config(g, C.byref(cfg)), "slab_group_set_config")
+
+
+def slab_group_reset(g: int, stream=None) -> None:
+    _check(load_library().slab_group_reset(g, _stream(stream)), "slab_group_reset")
+
+
+def _starts(op_start, ntables=None):
+    return _dptr(op_start, 4, op_start.numel(), "op_start")
+
+
+def slab_group_insert(g: int, op_start, keys, values, found=None, stream=None) -> None:
+    n = keys.numel()
+    _check(load_library().slab_group_insert(g, _starts(op_start), _dptr(keys, 4, n, "keys"),
+                                            _dptr(values, 4, n, "values", nullable=True),
+                                            _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)),
+           "slab_group_insert")
+
+
+def slab_group_delete(g: int, op_start, keys, found=None, stream=None) -> None:
+    n = keys.numel()
+    _check(load_library().slab_group_delete(g, _starts(op_start), _dptr(keys, 4, n, "keys"),
+                                            _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)),
+           "slab_group_delete")
+
+
+def slab_group_search(g: int, op_start, keys, values_out, found=None, stream=None) -> None:
+    n = keys.numel()
+    _check(load_library().slab_group_search(g, _starts(op_start), _dptr(keys, 4, n, "keys"),
+                                            _dptr(values_out, 4, n, "values_out"),
+                                            _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)),
+           "slab_group_search")
+
+
+def slab_group_mixed(g: int, op_start, ops, keys, values, results, found=None, stream=None) -> None:
+    n = keys.numel()
+    _check(load_library().slab_group_mixed(g, _starts(op_start), _dptr(ops, 1, n, "ops"), _dptr(keys, 4, n, "keys"),
+                                           _dptr(values, 4, n, "values", nullable=True),
+                                           _dptr(results, 4, n, "results"),
+                                           _dptr(found, 1, n, "found", nullable=True), n, _stream(stream)),
+           "slab_group_mixed")
+
+
+def slab_group_status(g: int, stream=None) -> tuple[int, int]:
+    flags = C.c_uint32(0)
+    rc = load_library().slab_group_status(g, _stream(stream), C.byref(flags))
+    if rc == SLAB_ERR_CUDA or rc == SLAB_ERR_INVALID_ARG:
+        raise SlabError(rc, "slab_group_status")
+    return rc, flags.value
 
 
 # ------------------------------------------------------------------ convenience

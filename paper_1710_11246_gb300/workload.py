@@ -229,5 +229,47 @@ def config4(seed: int = 0, n: int = 1 << 22, beta: float = 0.6, hit_rate: float 
                         np.empty(0, np.uint32))
 
 
+@dataclass
+class GroupWorkload:
+    """Many independent tables: per-table sizes, buckets and hash parameters, and
+    batches concatenated by table (op_start[i] = first op of table i)."""
+    sizes: np.ndarray
+    num_buckets: np.ndarray
+    hash_a: np.ndarray
+    hash_b: np.ndarray
+    op_start: np.ndarray
+    keys: np.ndarray
+    values: np.ndarray
+    search_start: np.ndarray
+    search_keys: np.ndarray
+    search_present: np.ndarray
+
+
+def group_workload(ntables: int, lo: int, hi: int, beta: float = 0.6, hit_rate: float = 0.5,
+                   seed: int = 0, sizes=None) -> GroupWorkload:
+    """`ntables` tables with sizes log-uniform in [lo, hi] (or the given sizes), each
+    with B = ceil(n / (15 beta)) and its own hash parameters; one search batch per
+    table of n queries at the hit rate."""
+    rng = np.random.default_rng([int(seed), 0x6A0])
+    if sizes is None:
+        sizes = np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), ntables))).astype(np.int64)
+    sizes = np.asarray(sizes, np.int64)
+    stream = KeyStream(seed + 0x5000)
+    B = np.array([buckets_for(max(int(n), 1), beta) for n in sizes], np.uint32)
+    ha = rng.integers(1, HASH_PRIME, ntables).astype(np.uint32)
+    hb = rng.integers(0, HASH_PRIME, ntables).astype(np.uint32)
+    keys, qk, qp = [], [], []
+    for n in sizes:
+        k = stream.take(int(n))
+        keys.append(k)
+        sb = search_batch(stream, k, int(n), hit_rate, rng)
+        qk.append(sb.keys)
+        qp.append(sb.present)
+    op_start = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint32)
+    allk = np.concatenate(keys).astype(np.uint32) if keys else np.empty(0, np.uint32)
+    return GroupWorkload(sizes, B, ha, hb, op_start, allk, values_for(allk), op_start.copy(),
+                         np.concatenate(qk).astype(np.uint32), np.concatenate(qp))
+
+
 CONFIG3_RATIOS = ((0.5, 0.5, 0.0), (0.2, 0.2, 0.6), (0.05, 0.05, 0.9))
 CONFIG2_BETAS = (0.2, 0.4, 0.6, 0.8, 1.0, 2.0)
