@@ -34,6 +34,7 @@ N_DELETE = 1 << 20
 N_MIXED = 1 << 20
 BETA = 0.6
 HIT = 0.5
+SERVING_KEYS, SERVING_REQUESTS, SERVING_POOL, SERVING_SLOT_OPS = 1 << 26, 8192, 1 << 22, 1 << 20
 MIXED_RATIOS = (0.2, 0.2, 0.6)
 POOL_SLABS = 1 << 20
 OPS_PER_STEP = N_KEYS + N_SEARCH + N_DELETE + N_MIXED
@@ -367,8 +368,11 @@ def sweep(args, device):
     def best(fn):
         return min(_time_ms(fn, stream, flush) for _ in range(reps))
 
+    def want(name):
+        return args.sweep in ("all", name)
+
     # bulk: build, search at 0/50/100 % hit, delete, for every beta
-    for beta in W.CONFIG2_BETAS:
+    for beta in (W.CONFIG2_BETAS if want("bulk") else ()):
         w = W.config2(beta, 0.5, args.seed)
         stream_k = W.KeyStream(args.seed)
         stream_k.take(N_KEYS + N_SEARCH)
@@ -413,6 +417,55 @@ def sweep(args, device):
         t.close()
         del snap
 
+    if want("slaballoc"):
+        slaballoc_sweep(device, stream, flush, reps)
+    if want("learned"):
+        learned_sweep(args, device, stream, flush)
+    if want("group"):
+        group_sweep(args, device, stream, flush)
+    if want("serving"):
+        serving_sweep(args, device, stream, flush)
+    if not want("mixed"):
+        return
+    # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
+    for ratios in W.CONFIG3_RATIOS:
+        w = W.config2(BETA, HIT, args.seed)
+        ks = W.KeyStream(args.seed)
+        ks.take(N_KEYS + N_SEARCH)
+        rng = np.random.default_rng([args.seed, 0xC0C0])
+        live = w.keys
+        batches = []
+        for _ in range(64):
+            mb, live = W.mixed_batch(ks, live, N_MIXED, ratios, rng)
+            batches.append((torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)))
+        t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 22)
+        h = t.handle
+        res = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+        with torch.cuda.stream(stream):
+            sh.slab_insert_batch(h, dev(w.keys), dev(w.values), None, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        for ops, keys, vals in batches:
+            ms.append(_time_ms(lambda: sh.slab_mixed_batch(h, ops, keys, vals, res, None, stream=stream),
+                               stream, flush))
+        rc, flags = t.status(stream)
+        tot = t.stats()
+        print(json.dumps({"sweep": "mixed", "ratios": ratios, "batches": 64, "batch_ops": N_MIXED,
+                          "unit": "Mops/s", "mean": round(64 * N_MIXED / (sum(ms) * 1e3), 1),
+                          "first_batch": round(N_MIXED / (ms[0] * 1e3), 1),
+                          "last_batch": round(N_MIXED / (ms[-1] * 1e3), 1),
+                          "final_slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4),
+                          "status": rc}), flush=True)
+        t.close()
+
+
+def slaballoc_sweep(device, stream, flush, reps):
+    """SlabAlloc microbenchmark (Sec. 5)."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
+
     # SlabAlloc: 2^24 single-slab allocations (one per lane), then 2^24 frees
     n = 1 << 24
     t = sh.SlabHash(8, 3, 4, 1 << 25)
@@ -430,6 +483,15 @@ def sweep(args, device):
                       "status": rc, "bitmaps_clear_after_free": bm_zero}), flush=True)
     t.close()
     del addrs
+
+
+
+def learned_sweep(args, device, stream, flush):
+    """Learned bucket function vs the universal hash on clustered keys."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
 
     # learned bucket function vs universal hash on clustered keys (2^22, beta = 0.6)
     w = W.config4(seed=args.seed)
@@ -458,6 +520,15 @@ def sweep(args, device):
         line["report"] = rep
         t.close()
     print(json.dumps(line), flush=True)
+
+
+
+def group_sweep(args, device, stream, flush):
+    """Groups of tables: per-table launches, one group launch, CUDA graph, autotuned."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
 
     # 512 independent tables, sizes log-uniform in [2^8, 2^18]: per-table launches vs
     # one group launch per batch vs the group step replayed from a CUDA graph, and the
@@ -508,36 +579,92 @@ def sweep(args, device):
                          "worst_mops": round(min(c.mops for c in cands), 1)}
     print(json.dumps(line), flush=True)
 
-    # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
-    for ratios in W.CONFIG3_RATIOS:
-        w = W.config2(BETA, HIT, args.seed)
-        ks = W.KeyStream(args.seed)
-        ks.take(N_KEYS + N_SEARCH)
-        rng = np.random.default_rng([args.seed, 0xC0C0])
-        live = w.keys
-        batches = []
-        for _ in range(64):
-            mb, live = W.mixed_batch(ks, live, N_MIXED, ratios, rng)
-            batches.append((torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)))
-        t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 22)
-        h = t.handle
-        res = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+
+
+def serving_sweep(args, device, stream, flush):
+    """Serving loop on one resident 2^26-pair table (beta = 0.6, universal hash):
+    requests of log-uniform size 1..2^16 with ops (0.1, 0.1, 0.8), admitted by free
+    SlabAlloc memory, overlapped on the server's slot streams. Lines: throughput at
+    saturation (every request queued at time 0) per slot count, p50 / p99 latency
+    under Poisson arrivals at fractions of the 8-slot saturation rate, and the plain
+    slab hash on the same ops as one mixed batch."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
+    R = SERVING_REQUESTS
+    tr = W.serving_trace(SERVING_KEYS, R, None, seed=args.seed)
+    total = int(tr.op_start[-1])
+    t = sh.SlabHash(tr.num_buckets, tr.hash_a, tr.hash_b, SERVING_POOL)
+    kb, vb = dev(tr.preload), dev(W.values_for(tr.preload))
+
+    def load():
         with torch.cuda.stream(stream):
-            sh.slab_insert_batch(h, dev(w.keys), dev(w.values), None, stream=stream)
+            sh.slab_reset(t.handle, stream)
+            sh.slab_insert_batch(t.handle, kb, vb, None, stream=stream)
         torch.cuda.synchronize()
-        ms = []
-        for ops, keys, vals in batches:
-            ms.append(_time_ms(lambda: sh.slab_mixed_batch(h, ops, keys, vals, res, None, stream=stream),
-                               stream, flush))
-        rc, flags = t.status(stream)
-        tot = t.stats()
-        print(json.dumps({"sweep": "mixed", "ratios": ratios, "batches": 64, "batch_ops": N_MIXED,
-                          "unit": "Mops/s", "mean": round(64 * N_MIXED / (sum(ms) * 1e3), 1),
-                          "first_batch": round(N_MIXED / (ms[0] * 1e3), 1),
-                          "last_batch": round(N_MIXED / (ms[-1] * 1e3), 1),
-                          "final_slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4),
-                          "status": rc}), flush=True)
-        t.close()
+
+    h_ops, h_keys, h_vals = (sh.pinned_copy(a) for a in (tr.ops, tr.keys, tr.values))
+
+    def serve(slots, arrival, flags):
+        load()
+        sv = sh.slab_server_create(t.handle, slots, SERVING_SLOT_OPS, flags=flags)
+        try:
+            out = sh.slab_server_run(sv, arrival, tr.op_start, h_ops, h_keys, h_vals, pinned_outputs=True)
+            st = sh.slab_server_get_stats(sv)
+        finally:
+            sh.slab_server_destroy(sv)
+        rc, _ = t.status()
+        return out, st, rc
+
+    line = {"sweep": "serving", "table_pairs": SERVING_KEYS, "num_buckets": tr.num_buckets,
+            "slot_ops": SERVING_SLOT_OPS,
+            "pool_slabs": t.info.pool_slabs, "requests": R, "ops": total, "ratios": [0.1, 0.1, 0.8],
+            "sizes": "log-uniform [1, 2^16]", "unit": "Mops/s"}
+    # the plain slab hash: the trace's ops as one mixed batch, inputs resident
+    ops_d, keys_d, vals_d = torch.from_numpy(tr.ops).to(device), dev(tr.keys), dev(tr.values)
+    res = torch.empty(total, dtype=torch.int32, device=device)
+    plain = []
+    for _ in range(3):
+        load()
+        plain.append(_time_ms(lambda: sh.slab_mixed_batch(t.handle, ops_d, keys_d, vals_d, res, None,
+                                                          stream=stream), stream, flush))
+    line["plain_one_batch"] = round(total / (min(plain) * 1e3), 1)
+    del ops_d, keys_d, vals_d, res
+    zero = np.zeros(R, np.uint64)
+    modes = {"copy": 0, "zero_copy": sh.SLAB_SERVER_ZERO_COPY}
+    sat = {}
+    for mode, flags in modes.items():
+        serve(8, zero, flags)  # warm-up
+        for slots in (1, 2, 4, 8, 16):
+            out, st, rc = serve(slots, zero, flags)
+            sat[(mode, slots)] = (out["makespan_ns"], rc, st["batches"])
+    line["saturated"] = {m: {str(k): round(total / v[0] * 1e3, 1) for (mm, k), v in sat.items() if mm == m}
+                         for m in modes}
+    line["saturated_batches"] = {m: {str(k): v[2] for (mm, k), v in sat.items() if mm == m} for m in modes}
+    mode = max(modes, key=lambda m: total / sat[(m, 8)][0])
+    rate8 = R / (sat[(mode, 8)][0] * 1e-9)
+    line["poisson_mode"] = mode
+    line["saturated_requests_per_s_8_slots"] = round(rate8)
+    rng = np.random.default_rng([args.seed, 0x9015])
+    gaps = rng.exponential(1.0, R)
+    line["poisson_8_slots"] = []
+    for frac in (0.01, 0.1, 0.5, 0.8):
+        rate = frac * rate8
+        arrival = np.floor(np.cumsum(gaps) * (1e9 / rate)).astype(np.uint64)
+        out, st, rc = serve(8, arrival, modes[mode])
+        lat, wait = out["latency_ns"] / 1e3, out["wait_ns"] / 1e3
+        line["poisson_8_slots"].append({
+            "load": frac, "offered_requests_per_s": round(rate), "mops": round(total / out["makespan_ns"] * 1e3, 1),
+            "p50_us": round(float(np.percentile(lat, 50)), 1), "p99_us": round(float(np.percentile(lat, 99)), 1),
+            "wait_p50_us": round(float(np.percentile(wait, 50)), 1),
+            "wait_p99_us": round(float(np.percentile(wait, 99)), 1),
+            "requests_per_batch": round(R / st["batches"], 2),
+            "deferred_slot": st["deferred_slot"], "deferred_memory": st["deferred_memory"],
+            "status": rc, "all_served": bool((out["status"] == 0).all())})
+    line["status"] = max(v[1] for v in sat.values())
+    print(json.dumps(line), flush=True)
+    t.close()
 
 
 def main():
@@ -552,8 +679,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
-    ap.add_argument("--sweep", action="store_true",
-                    help="print the beta / hit-rate, SlabAlloc and concurrent-batch lines instead")
+    ap.add_argument("--sweep", nargs="?", const="all", default=None,
+                    choices=["all", "bulk", "slaballoc", "learned", "group", "serving", "mixed"],
+                    help="print the sweep lines (all, or one section) instead of the step line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -51,7 +51,8 @@ enum slab_rc {
     SLAB_ERR_OUT_OF_SLABS = 3, /* SlabAlloc found no free slab */
     SLAB_ERR_ITER_LIMIT = 4,   /* an op hit the per-op iteration cap */
     SLAB_ERR_CUDA = 5,
-    SLAB_ERR_CORRUPT = 6       /* a list held a next pointer outside the pool */
+    SLAB_ERR_CORRUPT = 6,      /* a list held a next pointer outside the pool */
+    SLAB_ERR_BUSY = 7          /* serving: no free slot, or the request has not finished */
 };
 
 /* Bits of the device status word (see slab_status). */
@@ -334,6 +335,102 @@ int slab_group_mixed(slab_group *g, const uint32_t *d_op_start, const uint8_t *d
 /* Synchronize `stream`, then read and clear every table's status word; *h_flags
  * (nullable) receives their OR; the return code ranks them as slab_status does. */
 int slab_group_status(slab_group *g, void *stream, uint32_t *h_flags);
+
+/*
+ * Serving (a library extension; the paper benchmarks batches, not a request
+ * loop). A server keeps one table resident and runs mixed-op requests on it:
+ * it owns `slots` slots, each with its own CUDA stream, event, and pinned host
+ * and device staging for max_request_ops ops. Work on a slot is one batch:
+ * inputs to the device, one slab_mixed_batch, a one-block count of the
+ * allocated pool slabs, outputs back. Batches on different slots overlap on
+ * the device. slab_server_submit runs each request as its own batch;
+ * slab_server_run serves a whole arrival trace with continuous batching (every
+ * free slot takes all requests that have arrived, in order, as one batch).
+ *
+ * Admission by free SlabAlloc memory: a batch with k inserts (each links at
+ * most one new slab) is admitted only if
+ *     measured + reserved + k <= pool_high_water * pool_slabs,
+ * where `measured` is the latest count of allocated pool slabs (each batch
+ * counts the bitmaps after it ran, on its stream) and `reserved` sums the
+ * inserts of batches whose count has not come back. Admitted batches run
+ * concurrently (Sec. 6.3 concurrent semantics): a request's results equal its
+ * results alone whenever no key of it is inserted or deleted by another
+ * request in flight.
+ *
+ * The table must not be used by other calls while a server drives it, and a
+ * server is not thread-safe.
+ */
+#define SLAB_SERVER_MAX_SLOTS 64u
+#define SLAB_SERVER_MAX_REQUEST_OPS (1u << 24)
+typedef struct slab_server slab_server; /* opaque, library-owned */
+typedef struct slab_server_stats {
+    uint64_t submitted;       /* requests admitted */
+    uint64_t completed;       /* requests finished and handed back */
+    uint64_t batches;         /* batches launched (one per submitted request, several requests per
+                                 batch under slab_server_run) */
+    uint64_t deferred_slot;   /* submit calls, or trace requests at the head of the queue, that
+                                 found every slot busy */
+    uint64_t deferred_memory; /* head-of-queue requests held back by the pool bound while others ran */
+    uint64_t rejected_memory; /* requests refused: the pool bound failed with nothing in flight */
+    uint64_t pool_slabs;      /* the table's pool size */
+    uint64_t pool_measured;   /* latest allocated-slab count */
+    uint64_t pool_reserved;   /* inserts of requests whose count is outstanding */
+    uint32_t inflight;        /* slots holding a request */
+    uint32_t pad;
+} slab_server_stats;
+/* t: a table on the current device (it may already hold keys); 1 <= slots <=
+ * SLAB_SERVER_MAX_SLOTS; 1 <= max_request_ops <= SLAB_SERVER_MAX_REQUEST_OPS
+ * (a slot's capacity: the largest request, and the largest batch
+ * slab_server_run packs); 0 < pool_high_water <= 1; flags: 0 or
+ * SLAB_SERVER_ZERO_COPY. Allocates the slots and measures the pool in use.
+ * Errors: SLAB_ERR_INVALID_ARG for bad arguments or a table of another device;
+ * SLAB_ERR_CUDA when an allocation fails (nothing is kept). */
+#define SLAB_SERVER_ZERO_COPY 0x1u /* slab_server_run: kernels read and write page-locked, device-mapped
+                                      caller arrays in place instead of copying them */
+int slab_server_create(slab_table *t, uint32_t slots, uint32_t max_request_ops, double pool_high_water,
+                       uint32_t flags, slab_server **out);
+/* Waits for every slot's stream, then frees the server (not the table). */
+void slab_server_destroy(slab_server *sv);
+/* Admit one request of n ops (host arrays, copied before the call returns;
+ * op codes and semantics as slab_mixed_batch; h_values may be NULL in key-only
+ * mode). On SLAB_OK *ticket names it. SLAB_ERR_BUSY: every slot holds a
+ * request (collect one). SLAB_ERR_OUT_OF_SLABS: the pool bound refuses it now
+ * (retry after collecting, or it will never fit if nothing is in flight).
+ * Neither queues any work. SLAB_ERR_INVALID_ARG for n = 0 or n > max ops. */
+int slab_server_submit(slab_server *sv, const uint8_t *h_ops, const uint32_t *h_keys, const uint32_t *h_values,
+                       uint32_t n, uint64_t *ticket);
+/* Hand back a request's results (n uint32 as slab_mixed_batch's d_results, n
+ * found bytes; either pointer may be NULL) and free its slot. wait = 0 polls:
+ * SLAB_ERR_BUSY while it runs. SLAB_ERR_INVALID_ARG for an unknown ticket. */
+int slab_server_collect(slab_server *sv, uint64_t ticket, uint32_t *h_results, uint8_t *h_found, int wait);
+int slab_server_get_stats(slab_server *sv, slab_server_stats *out);
+/*
+ * Serve a whole arrival trace on the calling thread: request r arrives
+ * h_arrival_ns[r] nanoseconds after the call starts (non-decreasing) and owns
+ * ops [h_op_start[r], h_op_start[r + 1]) of h_ops / h_keys / h_values
+ * (h_op_start: n_requests + 1 entries, h_op_start[0] = 0; no request longer
+ * than max_request_ops). Continuous batching: whenever a slot is free, the
+ * requests that have arrived and are not yet running are packed in arrival
+ * order, up to max_request_ops ops and the pool bound, into one batch on it;
+ * a finished batch is retired as soon as its event fires. Data movement per
+ * batch: with SLAB_SERVER_ZERO_COPY and page-locked, device-mapped caller
+ * arrays (cudaHostAlloc / cudaHostRegister under unified addressing) the
+ * kernels read the inputs and write the results in place; otherwise batches of
+ * more than 8192 ops are copied by DMA straight between page-locked caller
+ * arrays and device buffers, and the rest (and all pageable arrays) go through
+ * the slot's pinned staging with one copy each way. Outputs (host, indexed like the
+ * inputs; every pointer but h_status and h_arrival_ns/h_op_start nullable):
+ * h_results / h_found per op; h_latency_ns[r] = retirement time - arrival;
+ * h_wait_ns[r] = admission time - arrival; h_status[r] = SLAB_OK, or
+ * SLAB_ERR_OUT_OF_SLABS for a request the pool could not take with nothing in
+ * flight (not run; its outputs are untouched); *h_makespan_ns = time of the
+ * last retirement. Requires no outstanding tickets (else SLAB_ERR_BUSY). On a
+ * CUDA error every slot is drained and SLAB_ERR_CUDA is returned.
+ */
+int slab_server_run(slab_server *sv, uint64_t n_requests, const uint64_t *h_arrival_ns, const uint64_t *h_op_start,
+                    const uint8_t *h_ops, const uint32_t *h_keys, const uint32_t *h_values, uint32_t *h_results,
+                    uint8_t *h_found, uint64_t *h_latency_ns, uint64_t *h_wait_ns, uint8_t *h_status,
+                    uint64_t *h_makespan_ns);
 
 /* Human-readable name of a return code. Never NULL. */
 const char *slab_error_string(int rc);

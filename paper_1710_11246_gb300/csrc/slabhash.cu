@@ -262,6 +262,7 @@ const char* slab_error_string(int rc) {
         case SLAB_ERR_ITER_LIMIT: return "an op reached the iteration cap";
         case SLAB_ERR_CUDA: return "CUDA error";
         case SLAB_ERR_CORRUPT: return "a slab list held a next pointer outside the pool";
+        case SLAB_ERR_BUSY: return "no free serving slot, or the request has not finished";
         default: return "unknown error";
     }
 }

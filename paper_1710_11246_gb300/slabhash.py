@@ -18,7 +18,7 @@ from . import build as _build
 SLAB_MODE_KEY_VALUE, SLAB_MODE_KEY_ONLY = 0, 1
 SLAB_OP_INSERT, SLAB_OP_DELETE, SLAB_OP_SEARCH = 0, 1, 2
 SLAB_OK, SLAB_ERR_INVALID_ARG, SLAB_ERR_RESERVED_KEY = 0, 1, 2
-SLAB_ERR_OUT_OF_SLABS, SLAB_ERR_ITER_LIMIT, SLAB_ERR_CUDA, SLAB_ERR_CORRUPT = 3, 4, 5, 6
+SLAB_ERR_OUT_OF_SLABS, SLAB_ERR_ITER_LIMIT, SLAB_ERR_CUDA, SLAB_ERR_CORRUPT, SLAB_ERR_BUSY = 3, 4, 5, 6, 7
 SLAB_FLAG_RESERVED_KEY, SLAB_FLAG_OUT_OF_SLABS, SLAB_FLAG_ITER_LIMIT, SLAB_FLAG_BAD_POINTER = 1, 2, 4, 8
 SLAB_EMPTY_KEY = SLAB_NOT_FOUND = 0xFFFFFFFF
 SLAB_TOMBSTONE_KEY = 0xFFFFFFFE
@@ -34,7 +34,10 @@ EXPORTED = [
     "slab_group_create", "slab_group_destroy", "slab_group_table", "slab_group_get_config", "slab_group_set_config",
     "slab_group_reset", "slab_group_insert", "slab_group_delete", "slab_group_search", "slab_group_mixed",
     "slab_group_status",
+    "slab_server_create", "slab_server_destroy", "slab_server_submit", "slab_server_collect",
+    "slab_server_get_stats", "slab_server_run",
 ]
+SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY = 64, 1 << 24, 1
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
 MODEL_FLOATS = 2 + 2 * 1024
 
@@ -55,6 +58,14 @@ class SlabLearnReport(C.Structure):
     _fields_ = [("sample_size", C.c_uint32), ("use_learned", C.c_uint32), ("max_slabs_learned", C.c_uint32),
                 ("max_slabs_universal", C.c_uint32), ("mean_slabs_learned", C.c_double),
                 ("mean_slabs_universal", C.c_double)]
+
+
+class SlabServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
+                ("deferred_slot", C.c_uint64),
+                ("deferred_memory", C.c_uint64), ("rejected_memory", C.c_uint64), ("pool_slabs", C.c_uint64),
+                ("pool_measured", C.c_uint64), ("pool_reserved", C.c_uint64), ("inflight", C.c_uint32),
+                ("pad", C.c_uint32)]
 
 
 class SlabError(RuntimeError):
@@ -114,6 +125,12 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_group_search": (i32, [vp, vp, vp, vp, vp, u32, vp]),
             "slab_group_mixed": (i32, [vp, vp, vp, vp, vp, vp, vp, u32, vp]),
             "slab_group_status": (i32, [vp, vp, C.POINTER(u32)]),
+            "slab_server_create": (i32, [vp, u32, u32, C.c_double, u32, C.POINTER(vp)]),
+            "slab_server_destroy": (None, [vp]),
+            "slab_server_submit": (i32, [vp, vp, vp, vp, u32, C.POINTER(u64)]),
+            "slab_server_collect": (i32, [vp, u64, vp, vp, i32]),
+            "slab_server_get_stats": (i32, [vp, C.POINTER(SlabServerStats)]),
+            "slab_server_run": (i32, [vp, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.POINTER(u64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -397,6 +414,102 @@ def slab_group_status(g: int, stream=None) -> tuple[int, int]:
     if rc == SLAB_ERR_CUDA or rc == SLAB_ERR_INVALID_ARG:
         raise SlabError(rc, "slab_group_status")
     return rc, flags.value
+
+
+# ------------------------------------------------------------------ serving
+def _hptr(a, dtype, n: int, name: str, nullable: bool = False):
+    """Host pointer of a contiguous numpy array of `dtype` with at least n elements."""
+    import numpy as np
+    if a is None:
+        if nullable:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
+        raise ValueError(f"{name} must be a contiguous numpy array of {np.dtype(dtype).name}")
+    if a.size < n:
+        raise ValueError(f"{name} holds {a.size} elements, needs {n}")
+    return a.ctypes.data if a.size else None
+
+
+def slab_server_create(t: int, slots: int, max_request_ops: int, pool_high_water: float = 0.9,
+                       flags: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load_library().slab_server_create(t, slots, max_request_ops, float(pool_high_water), flags,
+                                             C.byref(h)), "slab_server_create")
+    return h.value
+
+
+def slab_server_destroy(sv: int) -> None:
+    load_library().slab_server_destroy(sv)
+
+
+def slab_server_submit(sv: int, ops, keys, values) -> tuple[int, int]:
+    """(rc, ticket): rc is SLAB_OK, SLAB_ERR_BUSY or SLAB_ERR_OUT_OF_SLABS; other codes raise."""
+    import numpy as np
+    n = len(keys)
+    ticket = C.c_uint64(0)
+    rc = load_library().slab_server_submit(sv, _hptr(ops, np.uint8, n, "ops"), _hptr(keys, np.uint32, n, "keys"),
+                                           _hptr(values, np.uint32, n, "values", True), n, C.byref(ticket))
+    if rc not in (SLAB_OK, SLAB_ERR_BUSY, SLAB_ERR_OUT_OF_SLABS):
+        raise SlabError(rc, "slab_server_submit")
+    return rc, ticket.value
+
+
+def slab_server_collect(sv: int, ticket: int, n: int, wait: bool = True):
+    """(results uint32[n], found uint8[n]), or None while the request runs (wait=False)."""
+    import numpy as np
+    res, found = np.empty(n, np.uint32), np.empty(n, np.uint8)
+    rc = load_library().slab_server_collect(sv, ticket, _hptr(res, np.uint32, n, "results"),
+                                            _hptr(found, np.uint8, n, "found"), int(bool(wait)))
+    if rc == SLAB_ERR_BUSY:
+        return None
+    _check(rc, "slab_server_collect")
+    return res, found
+
+
+def slab_server_get_stats(sv: int) -> dict:
+    st = SlabServerStats()
+    _check(load_library().slab_server_get_stats(sv, C.byref(st)), "slab_server_get_stats")
+    return {f: getattr(st, f) for f, _ in st._fields_ if f != "pad"}
+
+
+def pinned_empty(n: int, dtype):
+    """A numpy array of n elements in page-locked host memory (a pinned torch tensor's storage)."""
+    import numpy as np
+    tdt = {np.dtype(np.uint8): torch.uint8, np.dtype(np.uint32): torch.int32, np.dtype(np.uint64): torch.int64}
+    a = torch.empty(max(int(n), 1), dtype=tdt[np.dtype(dtype)], pin_memory=True).numpy().view(dtype)
+    return a[:n]
+
+
+def pinned_copy(a):
+    out = pinned_empty(len(a), a.dtype)
+    out[:] = a
+    return out
+
+
+def slab_server_run(sv: int, arrival_ns, op_start, ops, keys, values, pinned_outputs: bool = False) -> dict:
+    """Serve a trace (numpy arrays: uint64 arrival_ns[R], uint64 op_start[R + 1], uint8 ops, uint32 keys,
+    uint32 values or None). Returns results, found, latency_ns, wait_ns, status and makespan_ns.
+    With pinned_outputs the result arrays are page-locked, so the device writes them directly."""
+    import numpy as np
+    R = len(arrival_ns)
+    total = int(op_start[R]) if R else 0
+    if pinned_outputs:
+        res, found = pinned_empty(total, np.uint32), pinned_empty(total, np.uint8)
+    else:
+        res, found = np.zeros(total, np.uint32), np.zeros(total, np.uint8)
+    out = {"results": res, "found": found, "latency_ns": np.zeros(R, np.uint64), "wait_ns": np.zeros(R, np.uint64),
+           "status": np.zeros(R, np.uint8)}
+    mk = C.c_uint64(0)
+    rc = load_library().slab_server_run(
+        sv, R, _hptr(arrival_ns, np.uint64, R, "arrival_ns"), _hptr(op_start, np.uint64, R + 1, "op_start"),
+        _hptr(ops, np.uint8, total, "ops"), _hptr(keys, np.uint32, total, "keys"),
+        _hptr(values, np.uint32, total, "values", True), res.ctypes.data if total else None,
+        found.ctypes.data if total else None, out["latency_ns"].ctypes.data, out["wait_ns"].ctypes.data,
+        out["status"].ctypes.data, C.byref(mk))
+    _check(rc, "slab_server_run")
+    out["makespan_ns"] = mk.value
+    return out
 
 
 # ------------------------------------------------------------------ convenience

@@ -271,5 +271,65 @@ def group_workload(ntables: int, lo: int, hi: int, beta: float = 0.6, hit_rate: 
                          np.concatenate(qk).astype(np.uint32), np.concatenate(qp))
 
 
+@dataclass
+class ServingTrace:
+    """Requests for one resident table: request r arrives at arrival_ns[r] and owns
+    ops [op_start[r], op_start[r + 1]). The table is first loaded with `preload`."""
+    num_buckets: int
+    hash_a: int
+    hash_b: int
+    preload: np.ndarray
+    arrival_ns: np.ndarray  # uint64, non-decreasing
+    op_start: np.ndarray    # uint64, R + 1 entries
+    ops: np.ndarray         # uint8
+    keys: np.ndarray        # uint32
+    values: np.ndarray      # uint32
+
+
+def request_sizes(n_requests: int, max_size: int, rng: np.random.Generator) -> np.ndarray:
+    """Sizes log-uniform on [1, max_size]: floor(exp(U[0, ln(max_size + 1)))."""
+    return np.floor(np.exp(rng.uniform(0.0, np.log(max_size + 1), n_requests))).astype(np.int64).clip(1, max_size)
+
+
+def serving_trace(n_preload: int, n_requests: int, rate_per_s: float | None, beta: float = 0.6,
+                  ratios: tuple[float, float, float] = (0.1, 0.1, 0.8), max_size: int = 1 << 16,
+                  hit_rate: float = 0.5, seed: int = 0) -> ServingTrace:
+    """Poisson arrivals at `rate_per_s` (None: every request at time 0), log-uniform sizes,
+    op kinds drawn independently per op in `ratios`. Keys are disjoint across requests
+    for every op that changes the table: inserts are fresh keys, deletes take distinct
+    preloaded keys in order, searches hit the other preloaded keys (no request deletes
+    them) or miss with fresh keys. Every result is therefore independent of the order
+    in which requests run."""
+    rng = np.random.default_rng([int(seed), 0x5E7])
+    stream = KeyStream(seed + 0x7000)
+    a, b = hash_params(seed)
+    preload = stream.take(n_preload)
+    sizes = request_sizes(n_requests, max_size, rng)
+    total = int(sizes.sum())
+    u = rng.random(total)
+    fi, fd, _ = ratios
+    ops = np.where(u < fi, OP_INSERT, np.where(u < fi + fd, OP_DELETE, OP_SEARCH)).astype(np.uint8)
+    keys = np.empty(total, np.uint32)
+    ins, dele, srch = ops == OP_INSERT, ops == OP_DELETE, ops == OP_SEARCH
+    n_del = int(dele.sum())
+    if n_del >= n_preload:
+        raise ValueError("the trace deletes more keys than the table holds")
+    keys[ins] = stream.take(int(ins.sum()))
+    keys[dele] = preload[:n_del]
+    stable = preload[n_del:]
+    hit = srch & (rng.random(total) < hit_rate)
+    miss = srch & ~hit
+    n_hit = int(hit.sum())
+    keys[hit] = stable[np.arange(n_hit) % len(stable)]
+    keys[miss] = stream.take(int(miss.sum()))
+    values = np.where(ins, values_for(keys), np.uint32(0)).astype(np.uint32)
+    if rate_per_s is None:
+        arrival = np.zeros(n_requests, np.uint64)
+    else:
+        arrival = np.floor(np.cumsum(rng.exponential(1e9 / rate_per_s, n_requests))).astype(np.uint64)
+    op_start = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    return ServingTrace(buckets_for(n_preload, beta), a, b, preload, arrival, op_start, ops, keys, values)
+
+
 CONFIG3_RATIOS = ((0.5, 0.5, 0.0), (0.2, 0.2, 0.6), (0.05, 0.05, 0.9))
 CONFIG2_BETAS = (0.2, 0.4, 0.6, 0.8, 1.0, 2.0)

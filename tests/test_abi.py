@@ -51,8 +51,8 @@ def test_library_built_for_sm103a():
 
 
 def test_error_strings(lib):
-    for rc in range(7):
-        assert lib.slab_error_string(rc)
+    for rc in range(8):
+        assert lib.slab_error_string(rc) and lib.slab_error_string(rc) != b"unknown error"
     assert sh.slab_error_string(sh.SLAB_ERR_OUT_OF_SLABS) == "SlabAlloc pool exhausted"
 
 
@@ -65,6 +65,12 @@ def test_host_argument_checks(lib):
         assert lib.slab_create(*args, C.byref(h)) == sh.SLAB_ERR_INVALID_ARG, args
     assert lib.slab_insert_batch(None, None, None, None, 0, None) == sh.SLAB_ERR_INVALID_ARG
     assert lib.slab_status(None, None, None) == sh.SLAB_ERR_INVALID_ARG
+    sv = C.c_void_p()
+    assert lib.slab_server_create(None, 4, 1024, 0.9, 0, C.byref(sv)) == sh.SLAB_ERR_INVALID_ARG
+    assert lib.slab_server_submit(None, None, None, None, 1, None) == sh.SLAB_ERR_INVALID_ARG
+    assert lib.slab_server_collect(None, 1, None, None, 1) == sh.SLAB_ERR_INVALID_ARG
+    assert lib.slab_server_run(None, 0, None, None, None, None, None, None, None, None, None, None,
+                               None) == sh.SLAB_ERR_INVALID_ARG
 
 
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device path")
