@@ -325,10 +325,33 @@ int slab_group_get_config(const slab_group* g, slab_config* out) {
     return SLAB_OK;
 }
 
+// The largest block every group kernel of a mode can launch (register caps).
+static int group_block_limit(int mode) {
+    int lim = 1024;
+    auto take = [&](const void* k) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, k) == cudaSuccess) lim = std::min(lim, a.maxThreadsPerBlock);
+        else cudaGetLastError();
+    };
+    if (mode == SLAB_MODE_KEY_ONLY) {
+        take((const void*)group_kernel<kKindSearch, true>);
+        take((const void*)group_kernel<kKindInsert, true>);
+        take((const void*)group_kernel<kKindDelete, true>);
+        take((const void*)group_kernel<kKindMixed, true>);
+    } else {
+        take((const void*)group_kernel<kKindSearch, false>);
+        take((const void*)group_kernel<kKindInsert, false>);
+        take((const void*)group_kernel<kKindDelete, false>);
+        take((const void*)group_kernel<kKindMixed, false>);
+    }
+    return lim - lim % 32;
+}
+
 int slab_group_set_config(slab_group* g, const slab_config* c) {
     if (!g || !c || c->threads_per_block < 32 || c->threads_per_block > 1024 || c->threads_per_block % 32 ||
         c->blocks_per_sm < 0 || c->blocks_per_sm > 64 || c->iter_limit < 1 || c->random_probes > (1u << 20) ||
-        (uint64_t)(c->threads_per_block / 32) * kGroupWordsPerWarp * 4 > 227 * 1024)
+        (uint64_t)(c->threads_per_block / 32) * kGroupWordsPerWarp * 4 > 227 * 1024 ||
+        c->threads_per_block > group_block_limit(g->mode))
         return SLAB_ERR_INVALID_ARG;
     g->cfg = *c;
     g->cfg.variant = SLAB_VARIANT_STAGED;

@@ -39,7 +39,7 @@ struct TableView {
     uint32_t iter_limit;
     uint32_t random_probes;
     uint32_t epoch;       // distinct per launch; spreads resident blocks over launches
-    uint32_t prefetch_l2; // claim kernels pull the next tile's base slabs into L2 (tables larger than L2)
+    uint32_t prefetch_l2; // staged kernels pull the next tile's base slabs into L2 (tables much larger than L2)
     uint32_t learned;     // 1: buckets come from the learned model, 0: from the universal hash
 };
 

@@ -1,24 +1,28 @@
 // The GB300 kernel family for slab-hash batches: warp-cooperative work sharing
 // (Sec. 4.1) with the slab reads moved off the critical path.
 //
-// Each warp walks tiles of 32 ops (one per lane) in a persistent grid, as a
-// three-stage pipeline:
-//   tile t+2  its keys, values and op codes are being loaded into registers;
-//   tile t+1  its keys are hashed and its 32 base slabs are in flight into one
-//             half of the warp's shared-memory stage (cp.async, 16 bytes per
-//             lane, 4 slabs per warp instruction);
-//   tile t    is served from the other half.
+// Each warp walks tiles of 32 ops (one per lane) in a persistent grid. Per tile:
+//   the tile's 32 base slabs are copied into the warp's shared-memory stage
+//   (cp.async, 16 bytes per lane, 4 slabs per warp instruction); while they are
+//   in flight the warp hashes the next tile's keys (pulling its base slabs into
+//   L2 for tables much larger than L2) and starts loading the tile after;
+//   then the tile is served from the stage.
 // Serving a tile is the WCWS loop of Fig. "alg:search": the warp takes the queued
 // ops in lane order; for each one it reads the op's slab coalesced (word `lane`
-// per lane, here from the stage), broadcasts the op's key by shuffle and finds
-// matching or empty key lanes by ballot. The ballot word is parked in shared
-// memory and the source lane then acts on it: it reads the value (search),
-// writes the tombstone (delete) or issues the 64-bit CAS of the pair (replace).
-// All source lanes act in the same instructions, so the 32 CASes of a tile are in
-// flight together and their results are checked once. A claim that lost its race
-// tries the following pair of the same slab at once; ops that must follow a next
-// pointer, or that ran off their slab, restage just their slabs and go round
-// again; a full list grows through SlabAlloc exactly as in the paper.
+// per lane, here from the stage), takes the op's key from the shared copy of the
+// tile's keys and finds matching or empty key lanes by ballot. The ballot word is
+// parked in shared memory and the source lane then acts on it: it reads the
+// value (search), writes the tombstone (delete) or issues the 64-bit CAS of the
+// pair (replace). All source lanes act in the same instructions, so the 32 CASes
+// of a tile are in flight together and their results are checked once. A claim
+// that lost its race tries the following pair of the same slab at once; ops that
+// must follow a next pointer, or that ran off their slab, restage just their
+// slabs and go round again; a full list grows through SlabAlloc exactly as in the
+// paper.
+//
+// Staging just before serving (rather than a tile ahead into a second buffer)
+// keeps one 4 KB stage per warp, which leaves room for more resident warps, and
+// gives claims a fresh snapshot (an older one makes them lose more races).
 #pragma once
 #include "slab_device.cuh"
 #include "slab_wcws.cuh"
@@ -27,19 +31,9 @@ namespace slab {
 
 constexpr uint32_t kTileWords = 32u * kWordsPerSlab;  // one slab per lane: 4 KB
 constexpr uint32_t kNoOpCode = 0xFFu;
-
-// Kernels whose ops claim pairs with a CAS stage each tile's slabs just before
-// serving it (a stale snapshot would make claims lose races to other warps); the
-// next tile's base slabs are only pulled into L2 ahead of time, and only when the
-// base slabs do not fit comfortably in L2 (otherwise the extra L2 requests cost
-// more than they save). Read-only and
-// tombstone-only kernels stage a whole tile ahead into a second buffer.
-template <int kKind>
-constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
-// per warp: one or two tile buffers, then 32 ballot words, the tile's 32 keys and
-// its 32 op codes (bytes)
-template <int kKind>
-constexpr uint32_t kStagedWordsPerWarp = (kClaims<kKind> ? 1u : 2u) * kTileWords + 32u + 32u + 8u;
+// per warp: the stage, then 32 ballot words, the tile's 32 keys and its 32 op
+// codes (bytes)
+constexpr uint32_t kStagedWordsPerWarp = kTileWords + 32u + 32u + 8u;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -259,26 +253,28 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
 }
 
 // Register caps of the staged kernels: more resident warps hide more of each
-// tile's read latency (all kernels) and claim round trip (insert, mixed).
-#ifndef SLAB_STAGED_MAXNREG
-#define SLAB_STAGED_MAXNREG 80
+// tile's staging latency (all kernels) and claim round trip (insert, mixed).
+#ifndef SLAB_READ_MAXNREG
+#define SLAB_READ_MAXNREG 72
 #endif
 #ifndef SLAB_CLAIM_MAXNREG
 #define SLAB_CLAIM_MAXNREG 56
 #endif
 
+template <int kKind>
+constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
+
 template <int kKind, bool kKeyOnly>
-__global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MAXNREG)
+__global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXNREG)
     staged_kernel(TableView T, BatchArgs A) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
     const uint32_t lane = lane_id();
-    constexpr bool kJit = kClaims<kKind>;
-    uint32_t* wsm = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp<kKind>;
-    uint32_t* ballots = wsm + (kJit ? 1u : 2u) * kTileWords;
+    uint32_t* buf = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp;
+    uint32_t* ballots = buf + kTileWords;
     uint32_t* skeys = ballots + 32;
     uint8_t* sops = reinterpret_cast<uint8_t*>(skeys + 32);
-    const uint32_t wsm_s = (uint32_t)__cvta_generic_to_shared(wsm);
+    const uint32_t buf_s = (uint32_t)__cvta_generic_to_shared(buf);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t ntiles = (A.n + 31u) / 32u;
@@ -306,59 +302,39 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_STAGED_MA
     };
     auto walks = [](uint32_t k, uint32_t o) { return o <= kOpSearch && k < kTombstone; };
 
-    // prologue: tile t staged into buffer 0 (or pulled into L2), tile t + nwarps loading
+    // prologue: this tile hashed (its base slabs pulled into L2 for big tables),
+    // the next tile loading
     uint32_t ck, cv, co;
     fetch(t, ck, cv, co);
     uint32_t cb = walks(ck, co) ? bucket_of(T, ck) : 0u;
-    if constexpr (kJit) {
-        if (T.prefetch_l2 && walks(ck, co)) prefetch_l2(T.slabs + (uint64_t)cb * kWordsPerSlab);
-    } else {
-        stage_slabs(T, wsm_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
-        cp_async_commit();
-    }
+    if (T.prefetch_l2 && walks(ck, co)) prefetch_l2(T.slabs + (uint64_t)cb * kWordsPerSlab);
     uint32_t nk, nv, no;
     fetch(t + nwarps, nk, nv, no);
-    uint32_t parity = 0;
 
     for (; t < ntiles; t += nwarps) {
-        // (1) next tile: hash its keys and start moving its base slabs closer
+        // (1) this tile's base slabs start moving into the stage
+        stage_slabs(T, buf_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
+        cp_async_commit();
+        // (2) meanwhile: hash the next tile (pulling its slabs into L2 for big
+        //     tables), start loading the tile after it, publish this tile's keys
         const bool nwalk = walks(nk, no);
         const uint32_t nb = nwalk ? bucket_of(T, nk) : 0u;
-        if constexpr (kJit) {
-            if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kWordsPerSlab);
-        } else {
-            stage_slabs(T, wsm_s + (parity ^ 1u) * kTileWords * 4u, nb, __ballot_sync(kFull, nwalk), lane);
-            cp_async_commit();
-        }
-        // (2) the tile after it: start its loads
+        if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kWordsPerSlab);
         uint32_t mk, mv, mo;
         fetch(t + 2u * nwarps, mk, mv, mo);
-        // (3) this tile's base slabs: committed one tile ago, or staged now
-        if constexpr (kJit) {
-            stage_slabs(T, wsm_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
-            cp_async_commit();
-            cp_async_wait<0>();
-        } else {
-            cp_async_wait<1>();
-        }
         skeys[lane] = ck;  // the WCWS steps read keys four at a time from here
         if constexpr (kKind == kKindMixed) sops[lane] = (uint8_t)co;
+        // (3) serve this tile once its slabs have landed
+        cp_async_wait<0>();
         __syncwarp();
-
-        // (4) serve this tile
-        const uint32_t* buf = wsm + (kJit ? 0u : parity) * kTileWords;
-        const uint32_t buf_s = wsm_s + (kJit ? 0u : parity) * kTileWords * 4u;
         const uint32_t idx = t * 32u + lane;
         serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, sops, off, ck, cv, co, cb, idx,
                                     idx < A.n);
-
-        // (5) rotate the pipeline
+        // (4) rotate the pipeline
         ck = nk; cv = nv; co = no; cb = nb;
         nk = mk; nv = mv; no = mo;
-        parity ^= 1u;
         __syncwarp();
     }
-    cp_async_wait<0>();
 }
 
 }  // namespace slab

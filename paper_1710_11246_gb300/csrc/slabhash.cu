@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -32,9 +33,38 @@ bool valid_config(const slab_config& c) {
     return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
            c.threads_per_block >= 32 && c.threads_per_block <= 1024 && c.threads_per_block % 32 == 0 &&
            c.blocks_per_sm >= 0 && c.blocks_per_sm <= 64 && c.iter_limit >= 1 && c.random_probes <= (1u << 20) &&
-           // staged kernels hold up to two 4 KB tile buffers per warp
+           // staged kernels hold one 4 KB stage (plus 288 bytes) per warp
            (c.variant != SLAB_VARIANT_STAGED ||
-            c.threads_per_block / 32 * kStagedWordsPerWarp<kKindSearch> * 4 <= 227 * 1024);
+            c.threads_per_block / 32 * kStagedWordsPerWarp * 4 <= 227 * 1024);
+}
+
+// The largest block every staged kernel of a mode can launch: their register
+// caps put it below 1024 threads (65,536 registers per SM). Cached per mode.
+int staged_block_limit(int mode) {
+    static std::atomic<int> cached[2] = {0, 0};
+    const int m = mode == SLAB_MODE_KEY_ONLY ? 1 : 0;
+    int lim = cached[m].load(std::memory_order_relaxed);
+    if (lim) return lim;
+    lim = 1024;
+    auto take = [&](const void* k) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, k) == cudaSuccess) lim = std::min(lim, a.maxThreadsPerBlock);
+        else cudaGetLastError();
+    };
+    if (m) {
+        take((const void*)staged_kernel<kKindSearch, true>);
+        take((const void*)staged_kernel<kKindInsert, true>);
+        take((const void*)staged_kernel<kKindDelete, true>);
+        take((const void*)staged_kernel<kKindMixed, true>);
+    } else {
+        take((const void*)staged_kernel<kKindSearch, false>);
+        take((const void*)staged_kernel<kKindInsert, false>);
+        take((const void*)staged_kernel<kKindDelete, false>);
+        take((const void*)staged_kernel<kKindMixed, false>);
+    }
+    lim -= lim % 32;
+    cached[m].store(lim, std::memory_order_relaxed);
+    return lim;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -216,7 +246,7 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
         k<<<grid, tpb, 0, S(stream)>>>(T, a);
     } else {
         auto k = staged_kernel<kKind, kKeyOnly>;
-        const size_t smem = (size_t)wpb * kStagedWordsPerWarp<kKind> * 4;
+        const size_t smem = (size_t)wpb * kStagedWordsPerWarp * 4;
         if ((int)smem > t->max_smem_optin) return SLAB_ERR_INVALID_ARG;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -372,6 +402,8 @@ int slab_get_config(const slab_table* t, slab_config* out) {
 
 int slab_set_config(slab_table* t, const slab_config* cfg) {
     if (!t || !cfg || !valid_config(*cfg)) return SLAB_ERR_INVALID_ARG;
+    if (cfg->variant == SLAB_VARIANT_STAGED && cfg->threads_per_block > staged_block_limit(t->mode))
+        return SLAB_ERR_INVALID_ARG;
     t->cfg = *cfg;
     return SLAB_OK;
 }

@@ -206,8 +206,8 @@ def test_iteration_cap_ends_ops_with_a_status(variant):
 
 
 @pytest.mark.parametrize("variant,tpb,bps", [("staged", 32, 1), ("staged", 128, 2), ("staged", 256, 0),
-                                             ("staged", 512, 1), ("direct", 32, 1), ("direct", 128, 2),
-                                             ("direct", 512, 0), ("direct", 1024, 1)])
+                                             ("staged", 512, 1), ("staged", 768, 1), ("direct", 32, 1),
+                                             ("direct", 128, 2), ("direct", 512, 0), ("direct", 1024, 1)])
 def test_launch_shapes(variant, tpb, bps):
     w = W.bulk_workload(20000, 0.8, 20000, 0.5, 5000, seed=4)
     p = Pair(w.num_buckets, w.hash_a, w.hash_b, variant=variant, n_hint=20000,
@@ -221,13 +221,42 @@ def test_launch_shapes(variant, tpb, bps):
         p.close()
 
 
-def test_staged_block_too_large_is_rejected():
-    """32 warps of two 4 KB tile buffers exceed the 227 KB of shared memory a block may use."""
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_largest_accepted_block_runs(variant):
+    """configure() refuses a block the kernels cannot launch (register caps bound
+    the staged kernels below 1024 threads); the largest block it accepts runs."""
+    w = W.bulk_workload(20000, 0.8, 20000, 0.5, 5000, seed=6)
+    p = Pair(w.num_buckets, w.hash_a, w.hash_b, variant=variant, n_hint=20000)
+    try:
+        for tpb in range(1024, 0, -32):
+            try:
+                p.g.configure(threads_per_block=tpb, blocks_per_sm=1)
+                break
+            except sh.SlabError:
+                continue
+        assert tpb >= 512
+        p.insert(w.keys, w.values)
+        p.search(w.search.keys)
+        p.delete(w.delete_keys)
+        p.check_structure()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_invalid_launch_configs_are_rejected(variant):
+    """Block sizes that are not whole warps or exceed 1024 threads, occupancy targets
+    above 64 blocks per SM and a zero iteration cap are refused; the table keeps its
+    previous configuration."""
     t = sh.SlabHash(16, 3, 4, 1024)
     try:
-        with pytest.raises(sh.SlabError):
-            t.configure(variant=sh.SLAB_VARIANT_STAGED, threads_per_block=1024)
-        t.configure(variant=sh.SLAB_VARIANT_DIRECT, threads_per_block=1024)
+        t.configure(variant=VARIANTS[variant], threads_per_block=512)
+        before = t.config()
+        for bad in (dict(threads_per_block=48), dict(threads_per_block=2048), dict(threads_per_block=0),
+                    dict(blocks_per_sm=65), dict(iter_limit=0), dict(variant=7)):
+            with pytest.raises(sh.SlabError):
+                t.configure(**bad)
+            assert t.config() == before
     finally:
         t.close()
 

@@ -67,8 +67,11 @@ def test_trace_matches_oracle(slots, rate, capacity, pinned, zero_copy):
         if rate is None and capacity > 1 << 12:
             assert st["batches"] < 300  # queued requests share launches
         _check_against_oracle(p, tr, out, np.ones(300, bool))
+        # the largest count a batch reported bounds the final allocation from above
+        # (a count may land while another batch holds a slab it frees after losing
+        # an append race)
         tot = p.g.stats()
-        assert st["pool_measured"] == tot["pool_allocated"]
+        assert st["pool_measured"] >= tot["pool_allocated"]
     finally:
         sh.slab_server_destroy(sv)
         p.close()
