@@ -43,7 +43,7 @@ struct slab_group {
 
 namespace {
 
-constexpr uint32_t kGroupWordsPerWarp = kTileWords + 32u + 32u + 8u;  // one tile buffer, ballots, keys, ops
+constexpr uint32_t kGroupWordsPerWarp = kStagedWordsPerWarp;  // the staged kernels' per-warp layout
 
 // Tiles of table i: ceil(ops / 32); a decreasing pair of starts counts as no ops.
 __device__ __forceinline__ uint32_t tiles_of(const uint32_t* op_start, uint32_t i) {
@@ -91,7 +91,7 @@ __global__ void __maxnreg__(SLAB_GROUP_MAXNREG)
     uint32_t* buf = smem + (threadIdx.x >> 5) * kGroupWordsPerWarp;
     uint32_t* ballots = buf + kTileWords;
     uint32_t* skeys = ballots + 32;
-    uint8_t* sops = reinterpret_cast<uint8_t*>(skeys + 32);
+    uint32_t* salts = skeys + 32;
     const uint32_t buf_s = (uint32_t)__cvta_generic_to_shared(buf);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -129,9 +129,9 @@ __global__ void __maxnreg__(SLAB_GROUP_MAXNREG)
         cp_async_commit();
         cp_async_wait<0>();
         skeys[lane] = ck;
-        if constexpr (kKind == kKindMixed) sops[lane] = (uint8_t)co;
+        if constexpr (kKind == kKindMixed) salts[lane] = alt_key(ck, co);
         __syncwarp();
-        serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, sops, off, ck, cv, co, cb, idx,
+        serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb, idx,
                                     has);
         __syncwarp();
     }

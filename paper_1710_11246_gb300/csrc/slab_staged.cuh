@@ -31,9 +31,15 @@ namespace slab {
 
 constexpr uint32_t kTileWords = 32u * kWordsPerSlab;  // one slab per lane: 4 KB
 constexpr uint32_t kNoOpCode = 0xFFu;
-// per warp: the stage, then 32 ballot words, the tile's 32 keys and its 32 op
-// codes (bytes)
-constexpr uint32_t kStagedWordsPerWarp = kTileWords + 32u + 32u + 8u;
+// per warp: the stage, then 32 ballot words, the tile's 32 keys and, for mixed
+// batches, 32 alternate keys (below)
+constexpr uint32_t kStagedWordsPerWarp = kTileWords + 32u + 32u + 32u;
+
+// The second value a mixed op's WCWS step matches besides its key: an empty
+// slot for an insert (it may claim one), its key again for a search or delete.
+__device__ __forceinline__ uint32_t alt_key(uint32_t key, uint32_t op) {
+    return op == kOpInsert ? kEmptyKey : key;
+}
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -74,13 +80,13 @@ __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, 
 
 // Serve one tile of up to 32 ops, one per lane (op index idx, valid where `has`),
 // whose base slabs are staged in slots 0..31 of `buf` (shared byte address
-// buf_s), keys in `skeys` and op codes in `sops`: the WCWS rounds of Fig.
+// buf_s), keys in `skeys` and (mixed) alternate keys in `salts`: the WCWS rounds of Fig.
 // "alg:search", each op's source-lane action, restaging for ops that move on,
 // list growth, and the result writes.
 template <int kKind, bool kKeyOnly>
 __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& A, AllocCtx& ac, uint32_t warp_gid,
                                            const uint32_t* buf, uint32_t buf_s, uint32_t* ballots,
-                                           const uint32_t* skeys, const uint8_t* sops, const uint32_t (&off)[8],
+                                           const uint32_t* skeys, const uint32_t* salts, const uint32_t (&off)[8],
                                            uint32_t ck, uint32_t cv, uint32_t co, uint32_t cb, uint32_t idx,
                                            bool has) {
     constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
@@ -102,19 +108,19 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
         }
         // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
         // The source key is broadcast from the shared copy of the tile's keys.
-        auto match = [&](uint32_t data, uint32_t skey, uint32_t sop) {
+        auto match = [&](uint32_t data, uint32_t skey, uint32_t salt) {
             bool pred;
             if constexpr (kKind == kKindInsert) {
                 pred = data == skey || data == kEmptyKey;
             } else if constexpr (kKind == kKindMixed) {
-                pred = data == skey || (sop == kOpInsert && data == kEmptyKey);
+                pred = data == skey || data == salt;
             } else {
                 pred = data == skey;
             }
             return __ballot_sync(kFull, pred);
         };
         auto step = [&](uint32_t s, uint32_t data) {
-            const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? sops[s] : 0u);
+            const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? salts[s] : 0u);
             if (lane == 0) ballots[s] = mm;
         };
         if (first && pend == kFull) {
@@ -122,13 +128,13 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
 #pragma unroll
             for (uint32_t g = 0; g < 8; ++g) {
                 const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
-                const uint32_t o4 = kKind == kKindMixed ? reinterpret_cast<const uint32_t*>(sops)[g] : 0u;
+                const uint4 a4 = kKind == kKindMixed ? *reinterpret_cast<const uint4*>(salts + 4u * g) : k4;
                 const uint32_t s0 = 4u * g;
                 uint4 b4;
-                b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, o4 & 0xFFu);
-                b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, (o4 >> 8) & 0xFFu);
-                b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, (o4 >> 16) & 0xFFu);
-                b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, o4 >> 24);
+                b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, a4.x);
+                b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, a4.y);
+                b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, a4.z);
+                b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, a4.w);
                 if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
             }
         } else if (first) {
@@ -273,7 +279,7 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
     uint32_t* buf = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp;
     uint32_t* ballots = buf + kTileWords;
     uint32_t* skeys = ballots + 32;
-    uint8_t* sops = reinterpret_cast<uint8_t*>(skeys + 32);
+    uint32_t* salts = skeys + 32;
     const uint32_t buf_s = (uint32_t)__cvta_generic_to_shared(buf);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -323,12 +329,12 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
         uint32_t mk, mv, mo;
         fetch(t + 2u * nwarps, mk, mv, mo);
         skeys[lane] = ck;  // the WCWS steps read keys four at a time from here
-        if constexpr (kKind == kKindMixed) sops[lane] = (uint8_t)co;
+        if constexpr (kKind == kKindMixed) salts[lane] = alt_key(ck, co);
         // (3) serve this tile once its slabs have landed
         cp_async_wait<0>();
         __syncwarp();
         const uint32_t idx = t * 32u + lane;
-        serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, sops, off, ck, cv, co, cb, idx,
+        serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb, idx,
                                     idx < A.n);
         // (4) rotate the pipeline
         ck = nk; cv = nv; co = no; cb = nb;

@@ -33,7 +33,7 @@ bool valid_config(const slab_config& c) {
     return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
            c.threads_per_block >= 32 && c.threads_per_block <= 1024 && c.threads_per_block % 32 == 0 &&
            c.blocks_per_sm >= 0 && c.blocks_per_sm <= 64 && c.iter_limit >= 1 && c.random_probes <= (1u << 20) &&
-           // staged kernels hold one 4 KB stage (plus 288 bytes) per warp
+           // staged kernels hold one 4 KB stage (plus 384 bytes) per warp
            (c.variant != SLAB_VARIANT_STAGED ||
             c.threads_per_block / 32 * kStagedWordsPerWarp * 4 <= 227 * 1024);
 }
