@@ -340,12 +340,40 @@ def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24):
     return best
 
 
+def random_cas_probe(device, footprint_bytes: int, n_ops: int = 1 << 22):
+    """Best random 64-bit atomicCAS rate (ops/s) on pair slots of lines at a footprint,
+    the buffer zeroed before each timing so most CASes claim an empty slot."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    lines = footprint_bytes // 128
+    buf = torch.zeros(lines * 16, dtype=torch.int64, device=device)
+    best = (0.0, None)
+    for oif in (2, 4, 8):
+        for tpb in (256, 512):
+            ts = []
+            for rep in range(4):
+                buf.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                sh.slab_probe_random_cas(buf, lines, n_ops, rep + 1, oif, tpb)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            rate = n_ops / (min(ts[1:]) * 1e-3)
+            if rate > best[0]:
+                best = (rate, {"ops_in_flight": oif, "threads_per_block": tpb})
+    del buf
+    return best
+
+
 # ---------------------------------------------------------------- sweep
 def _time_ms(fn, stream, flush):
+    """Device time of fn() on `stream`, after an L2 flush queued on the same stream."""
     import torch
-    flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        flush.zero_()
         e0.record(stream)
         fn()
         e1.record(stream)
@@ -737,9 +765,19 @@ def main():
             fp = r["table"].info.num_buckets * 128
             rate, cfg = random_line_probe(device, fp)
             rate_big, cfg_big = random_line_probe(device, 4 << 30)
+            cas_rate, cas_cfg = random_cas_probe(device, fp)
+            # CAS per op the method must issue: one pair claim per insert; deletes
+            # store a tombstone and searches only read
+            cas_per_op = {"build": 1.0, "search": 0.0, "delete": 0.0,
+                          "mixed": float((r["mb"].ops == W.OP_INSERT).mean())}
+            bound = {p: min(rate / (lines[p] / ops[p]),
+                            cas_rate / cas_per_op[p] if cas_per_op[p] else float("inf")) for p in ops}
             rl = {"footprint_bytes": fp, "glines_per_s": round(rate / 1e9, 3), "probe": cfg,
                   "glines_per_s_4GiB": round(rate_big / 1e9, 3),
-                  "per_phase_frac": {p: round(lines[p] / (mean[p] * 1e-3) / rate, 4) for p in ops}}
+                  "gcas_per_s": round(cas_rate / 1e9, 3), "cas_probe": cas_cfg, "cas_per_op": cas_per_op,
+                  "per_phase_frac": {p: round(lines[p] / (mean[p] * 1e-3) / rate, 4) for p in ops},
+                  "per_phase_bound_gops": {p: round(bound[p] / 1e9, 2) for p in ops},
+                  "per_phase_frac_line_cas": {p: round(ops[p] / (mean[p] * 1e-3) / bound[p], 4) for p in ops}}
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,

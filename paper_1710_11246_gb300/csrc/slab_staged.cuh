@@ -284,6 +284,10 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t ntiles = (A.n + 31u) / 32u;
+    // Launched as a programmatic dependent: let the next batch's grid be
+    // scheduled as our blocks retire, and touch no memory before the previous
+    // kernel on the stream has completed.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     uint32_t t = warp_gid;
     if (t >= ntiles) return;  // warp-uniform
 
@@ -293,6 +297,7 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
     for (uint32_t j = 0; j < 8; ++j) off[j] = (((lane >> 2) ^ j) << 2) | (lane & 3u);
 
     AllocCtx ac{kNoBlock, 0u, 0u};
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     auto fetch = [&](uint32_t tt, uint32_t& k, uint32_t& v, uint32_t& o) {
         const uint32_t i = tt * 32u + lane;

@@ -229,6 +229,9 @@ __global__ void free_kernel(TableView T, const uint32_t* addrs, uint32_t n) {
 }
 
 // ------------------------------------------------------------ batch launch
+#ifndef SLAB_PDL
+#define SLAB_PDL 1
+#endif
 template <int kKind, bool kKeyOnly>
 int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
     if (a.n == 0) return SLAB_OK;
@@ -257,7 +260,20 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
         const uint64_t tiles = (a.n + 31u) / 32u;
         const uint64_t want = (tiles + wpb - 1) / wpb;
         const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
-        k<<<(uint32_t)grid, tpb, smem, S(stream)>>>(T, a);
+        // Programmatic dependent launch: this grid may be scheduled while the
+        // previous kernel on the stream drains; the kernel waits for that kernel
+        // to complete (griddepcontrol.wait) before its first memory access.
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((uint32_t)grid);
+        lc.blockDim = dim3(tpb);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = S(stream);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = SLAB_PDL;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        if (cudaLaunchKernelEx(&lc, k, T, a) != cudaSuccess) return SLAB_ERR_CUDA;
     }
     return launch_rc();
 }
