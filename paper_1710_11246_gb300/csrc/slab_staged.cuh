@@ -64,17 +64,21 @@ __device__ __forceinline__ uint32_t swz(uint32_t s, uint32_t w) {
 
 // Copy, for every lane s in `mask`, the slab with unified index shfl(u, s)
 // (base slab b -> b, pool unit a -> B + a) into slot s of the stage at byte
-// address `stage`: lanes 8g..8g+7 move one slab as eight 16-byte pieces.
+// address `stage`: lanes 8g..8g+7 move one slab as eight 16-byte pieces, slots
+// g, g + 4, ..., g + 28 in turn. Slot 4j + g has (4j + g) mod 8 = 4 (j mod 2) + g,
+// so a lane's swizzled destinations take two forms, 512 bytes apart per j.
 __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, uint32_t u, uint32_t mask,
                                             uint32_t lane) {
-    const uint32_t c = lane & 7u;
+    const uint32_t g = lane >> 3, c = lane & 7u;
+    const uint32_t* src = T.slabs + c * 4u;  // this lane's 16-byte piece of slab 0
+    const uint32_t dst_even = stage + g * 128u + ((c ^ g) << 4);
+    const uint32_t dst_odd = stage + g * 128u + ((c ^ (g | 4u)) << 4);
+    const uint32_t mg = mask >> g;
 #pragma unroll
     for (uint32_t j = 0; j < 8; ++j) {
-        const uint32_t s = 4u * j + (lane >> 3);
-        const uint32_t us = __shfl_sync(kFull, u, s);
-        if ((mask >> s) & 1u)
-            cp_async_16(stage + (s * 32u + ((c ^ (s & 7u)) << 2)) * 4u,
-                                T.slabs + (uint64_t)us * kWordsPerSlab + c * 4u);
+        const uint32_t us = __shfl_sync(kFull, u, 4u * j + g);
+        if ((mg >> (4u * j)) & 1u)
+            cp_async_16(((j & 1u) ? dst_odd : dst_even) + j * 512u, src + (uint64_t)us * kWordsPerSlab);
     }
 }
 
