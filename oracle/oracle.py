@@ -67,6 +67,12 @@ def load_oracle(path: str | None = None):
             lib.oracle_learn_model.restype = C.c_uint64
             lib.oracle_learn_model.argtypes = [u32p, C.c_uint64, C.c_uint32, C.c_uint32, f32p]
             lib.oracle_chain_profile.argtypes = [C.c_void_p, u32p, C.c_uint64, u64p, u32p]
+            lib.oracle_set_multiset.restype = C.c_int
+            lib.oracle_set_multiset.argtypes = [C.c_void_p, C.c_int]
+            lib.oracle_search_all.argtypes = [C.c_void_p, u32p, C.c_uint64, C.c_uint32, u32p, u32p]
+            lib.oracle_delete_all.argtypes = [C.c_void_p, u32p, C.c_uint64, u32p]
+            lib.oracle_flush.restype = C.c_uint64
+            lib.oracle_flush.argtypes = [C.c_void_p]
             lib.oracle_check_alloc.restype = C.c_int
             lib.oracle_check_alloc.argtypes = [u32p, C.c_uint64, u32p, C.c_uint64, C.c_uint32, u64p]
             if path is not None:
@@ -176,6 +182,30 @@ class OracleTable:
 
     def utilization(self) -> float:
         return float(self.lib.oracle_utilization(self.h))
+
+    def set_multiset(self, on: bool = True):
+        """Make the (empty) table a multiset: inserts allow duplicates, deletes empty their slot."""
+        if self.lib.oracle_set_multiset(self.h, int(bool(on))) != 0:
+            raise ValueError("the table is not empty")
+
+    def search_all(self, keys, cap: int):
+        """(counts, values[n, cap]): every live instance of each key in list order."""
+        keys = _u32(keys)
+        counts = np.zeros(len(keys), np.uint32)
+        vals = np.full((len(keys), max(int(cap), 0)), 0xFFFFFFFF, np.uint32)
+        self.lib.oracle_search_all(self.h, _ptr(keys, C.c_uint32), len(keys), int(cap),
+                                   _ptr(counts, C.c_uint32), _ptr(vals, C.c_uint32) if vals.size else None)
+        return counts, vals
+
+    def delete_all(self, keys):
+        keys = _u32(keys)
+        counts = np.zeros(len(keys), np.uint32)
+        self.lib.oracle_delete_all(self.h, _ptr(keys, C.c_uint32), len(keys), _ptr(counts, C.c_uint32))
+        return counts
+
+    def flush(self) -> int:
+        """Compact every bucket (Sec. 4.3.4); returns the slabs released."""
+        return int(self.lib.oracle_flush(self.h))
 
     def export(self):
         """Live elements as (bucket, key, value) arrays in bucket / list order."""

@@ -8,10 +8,15 @@
  *
  * What it computes is the plain definition of the data structure, not the
  * GPU algorithm:
- *   - B buckets (Sec. 3.3). Each bucket is an insertion-ordered array of
- *     slots (key, value, live). A slot is "used" once written and stays used:
- *     deletion only clears `live` (a tombstone, Sec. 3.2 "Deletion"), and a
- *     tombstoned slot is never written again, so keys stay unique.
+ *   - B buckets (Sec. 3.3). Each bucket is an array of slot positions in list
+ *     order (key, value, state). In a set table (the default) a slot is
+ *     "used" once written and stays used: deletion turns it into a tombstone
+ *     (Sec. 3.2 "Deletion") that is never written again, so keys stay unique.
+ *     In a multiset table (duplicates allowed, Sec. 3.2 INSERT) deletion
+ *     empties the slot, and a later insert takes the first empty slot in list
+ *     order before appending.
+ *   - FLUSH (Sec. 4.3.4) compacts a bucket: its live elements keep their list
+ *     order and move to the front; tombstones and holes disappear.
  *   - h(k) = ((a k + b) mod p) mod B with plain 64-bit `%` (Sec. 3.3).
  *   - replace / delete / search with the set semantics of Sec. 3.2
  *     (replace = insert with uniqueness; delete and search act on the only
@@ -35,10 +40,12 @@
 
 enum { OR_OP_INSERT = 0, OR_OP_DELETE = 1, OR_OP_SEARCH = 2 };
 
+enum { OR_TOMB = 0, OR_LIVE = 1, OR_HOLE = 2 }; /* slot states */
+
 typedef struct {
     uint32_t key;
     uint32_t value;
-    uint8_t live;
+    uint8_t live; /* OR_LIVE, OR_TOMB (set tables) or OR_HOLE (emptied, multiset tables) */
 } or_slot;
 
 typedef struct {
@@ -53,6 +60,7 @@ typedef struct {
     float model[2 + 2 * 1024];
     uint32_t M;        /* data elements per slab: 15 (key-value) or 30 (key only) */
     int key_only;
+    int multiset;      /* duplicates allowed: INSERT instead of REPLACE, deletes empty their slot */
     uint64_t a, b, p;  /* universal hash parameters */
     or_bucket *bk;
     uint64_t live;     /* number of live elements */
@@ -263,11 +271,11 @@ void oracle_chain_profile(const or_table *t, const uint32_t *keys, uint64_t n, u
     *max = mx;
 }
 
-/* Position of the live slot holding `key` in bucket `bk`, or -1. */
+/* Position of the first live slot (in list order) holding `key`, or -1. */
 static int64_t find_live(const or_bucket *bk, uint32_t key)
 {
     for (uint32_t s = 0; s < bk->len; s++)
-        if (bk->s[s].live && bk->s[s].key == key) return (int64_t)s;
+        if (bk->s[s].live == OR_LIVE && bk->s[s].key == key) return (int64_t)s;
     return -1;
 }
 
@@ -287,8 +295,36 @@ static void append(or_bucket *bk, uint32_t key, uint32_t value)
     }
     bk->s[bk->len].key = key;
     bk->s[bk->len].value = value;
-    bk->s[bk->len].live = 1;
+    bk->s[bk->len].live = OR_LIVE;
     bk->len++;
+}
+
+/* Sec. 3.2 INSERT (multiset tables): S <- S U {<k,v>} with no uniqueness check; the
+ * pair goes into the first empty slot in list order (a hole left by a delete),
+ * else at the tail. Lines: the slabs read up to that slot. */
+static void op_insert_dup(or_table *t, uint32_t key, uint32_t value, uint64_t *lines)
+{
+    or_bucket *bk = &t->bk[oracle_bucket(t, key)];
+    if (t->key_only) value = 0;
+    uint32_t s = 0;
+    while (s < bk->len && bk->s[s].live != OR_HOLE) s++;
+    if (lines) *lines += (uint64_t)s / t->M + 1;
+    if (s < bk->len) {
+        bk->s[s].key = key;
+        bk->s[s].value = value;
+        bk->s[s].live = OR_LIVE;
+    } else {
+        append(bk, key, value);
+    }
+    t->live++;
+}
+
+/* Remove the element at position s: a tombstone in a set table, a hole (an empty
+ * slot later inserts may fill) in a multiset table (Sec. 3.2 "Deletion"). */
+static void kill(or_table *t, or_bucket *bk, uint32_t s)
+{
+    bk->s[s].live = t->multiset ? OR_HOLE : OR_TOMB;
+    t->live--;
 }
 
 /* Sec. 3.2 REPLACE: S <- (S - {<k,*>}) U {<k,v>}. If k is live, overwrite its value
@@ -312,15 +348,14 @@ static int op_replace(or_table *t, uint32_t key, uint32_t value, uint64_t *lines
     return 0;
 }
 
-/* Sec. 3.2 DELETE: remove the (only) live <k,v>; the slot becomes a tombstone.
- * Returns 1 if k was present. A miss reads every slab of the list. */
+/* Sec. 3.2 DELETE: remove the first live <k,v> in list order (the only one in a
+ * set table). Returns 1 if k was present. A miss reads every slab of the list. */
 static int op_delete(or_table *t, uint32_t key, uint64_t *lines)
 {
     or_bucket *bk = &t->bk[oracle_bucket(t, key)];
     int64_t s = find_live(bk, key);
     if (s >= 0) {
-        bk->s[s].live = 0;
-        t->live--;
+        kill(t, bk, (uint32_t)s);
         if (lines) *lines += (uint64_t)s / t->M + 1;
         return 1;
     }
@@ -328,7 +363,7 @@ static int op_delete(or_table *t, uint32_t key, uint64_t *lines)
     return 0;
 }
 
-/* Sec. 3.2 SEARCH: return the live <k,v> or "not found". */
+/* Sec. 3.2 SEARCH: return the first live <k,v> in list order, or "not found". */
 static int op_search(const or_table *t, uint32_t key, uint32_t *value, uint64_t *lines)
 {
     const or_bucket *bk = &t->bk[oracle_bucket(t, key)];
@@ -352,6 +387,7 @@ void oracle_insert(or_table *t, const uint32_t *keys, const uint32_t *values, ui
     for (uint64_t i = 0; i < n; i++) {
         int f = 0;
         if (keys[i] >= OR_KEY_LIMIT) t->reserved++;
+        else if (t->multiset) op_insert_dup(t, keys[i], values ? values[i] : 0u, lines);
         else f = op_replace(t, keys[i], values ? values[i] : 0u, lines);
         if (found) found[i] = (uint8_t)f;
     }
@@ -397,7 +433,8 @@ void oracle_mixed(or_table *t, const uint8_t *ops, const uint32_t *keys, const u
         } else if (keys[i] >= OR_KEY_LIMIT) {
             t->reserved++;
         } else if (ops[i] == OR_OP_INSERT) {
-            f = op_replace(t, keys[i], values ? values[i] : 0u, lines);
+            if (t->multiset) op_insert_dup(t, keys[i], values ? values[i] : 0u, lines);
+            else f = op_replace(t, keys[i], values ? values[i] : 0u, lines);
             r = f ? 0u : 1u;
         } else if (ops[i] == OR_OP_DELETE) {
             f = op_delete(t, keys[i], lines);
@@ -410,17 +447,20 @@ void oracle_mixed(or_table *t, const uint8_t *ops, const uint32_t *keys, const u
     }
 }
 
-/* Per-bucket used slots (live + tombstoned) and slab counts, plus totals
+/* Per-bucket used slots (live + tombstoned; holes are empty) and slab counts
+ * (the list spans every position ever written), plus totals
  * {live, used slots, slabs, reserved-key ops}. */
 void oracle_stats(const or_table *t, uint32_t *slots, uint32_t *slabs, uint64_t *totals)
 {
     uint64_t used = 0, nslabs = 0;
     for (uint32_t i = 0; i < t->B; i++) {
-        uint32_t len = t->bk[i].len;
-        uint64_t k = slabs_of(t, len);
-        if (slots) slots[i] = len;
+        const or_bucket *bk = &t->bk[i];
+        uint32_t u = 0;
+        for (uint32_t s = 0; s < bk->len; s++) u += bk->s[s].live != OR_HOLE;
+        uint64_t k = slabs_of(t, bk->len);
+        if (slots) slots[i] = u;
         if (slabs) slabs[i] = (uint32_t)k;
-        used += len;
+        used += u;
         nslabs += k;
     }
     if (totals) {
@@ -451,7 +491,7 @@ uint64_t oracle_export(const or_table *t, uint32_t *buckets, uint32_t *keys, uin
     for (uint32_t i = 0; i < t->B; i++) {
         const or_bucket *bk = &t->bk[i];
         for (uint32_t s = 0; s < bk->len; s++) {
-            if (!bk->s[s].live) continue;
+            if (bk->s[s].live != OR_LIVE) continue;
             if (c < cap) {
                 if (buckets) buckets[c] = i;
                 if (keys) keys[c] = bk->s[s].key;
@@ -461,6 +501,73 @@ uint64_t oracle_export(const or_table *t, uint32_t *buckets, uint32_t *keys, uin
         }
     }
     return c;
+}
+
+/* Make an empty table a multiset (duplicates allowed). Returns 0, or -1 if the
+ * table already holds elements. */
+int oracle_set_multiset(or_table *t, int on)
+{
+    for (uint32_t i = 0; i < t->B; i++)
+        if (t->bk[i].len) return -1;
+    t->multiset = on ? 1 : 0;
+    return 0;
+}
+
+/* Sec. 3.2 SEARCHALL: every live <k,*> in list order. counts[i] = the number of
+ * instances of keys[i]; their values (0 in key-only mode) go to
+ * values[i * cap + j] for j < min(counts[i], cap), the rest of the row untouched. */
+void oracle_search_all(const or_table *t, const uint32_t *keys, uint64_t n, uint32_t cap, uint32_t *counts,
+                       uint32_t *values)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint32_t c = 0;
+        if (keys[i] < OR_KEY_LIMIT) {
+            const or_bucket *bk = &t->bk[oracle_bucket(t, keys[i])];
+            for (uint32_t s = 0; s < bk->len; s++) {
+                if (bk->s[s].live != OR_LIVE || bk->s[s].key != keys[i]) continue;
+                if (c < cap && values) values[i * cap + c] = t->key_only ? 0u : bk->s[s].value;
+                c++;
+            }
+        }
+        if (counts) counts[i] = c;
+    }
+}
+
+/* Sec. 3.2 DELETEALL: remove every live <k,*>; counts[i] = how many. */
+void oracle_delete_all(or_table *t, const uint32_t *keys, uint64_t n, uint32_t *counts)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint32_t c = 0;
+        if (keys[i] >= OR_KEY_LIMIT) {
+            t->reserved++;
+        } else {
+            or_bucket *bk = &t->bk[oracle_bucket(t, keys[i])];
+            for (uint32_t s = 0; s < bk->len; s++)
+                if (bk->s[s].live == OR_LIVE && bk->s[s].key == keys[i]) {
+                    kill(t, bk, s);
+                    c++;
+                }
+        }
+        if (counts) counts[i] = c;
+    }
+}
+
+/* Sec. 4.3.4 FLUSH of every bucket: the live elements keep their list order and
+ * move to the front of the list, tombstones and holes disappear, and the list
+ * keeps max(1, ceil(live / M)) slabs. Returns the number of slabs released. */
+uint64_t oracle_flush(or_table *t)
+{
+    uint64_t released = 0;
+    for (uint32_t i = 0; i < t->B; i++) {
+        or_bucket *bk = &t->bk[i];
+        uint64_t before = slabs_of(t, bk->len);
+        uint32_t w = 0;
+        for (uint32_t s = 0; s < bk->len; s++)
+            if (bk->s[s].live == OR_LIVE) bk->s[w++] = bk->s[s];
+        bk->len = w;
+        released += before - slabs_of(t, w);
+    }
+    return released;
 }
 
 /*

@@ -368,4 +368,197 @@ def pin_learned_table_semantics(lib):
     assert int(learned_buckets(model, B, [0, 0xFFFFFFFD], lib=lib).max()) < B
 
 
+# ------------------------------------------------------------- multiset and flush
+class FlatMultiset:
+    """Sec. 3.2 with duplicates allowed, over one flat list in insertion order:
+    INSERT appends, DELETE removes the least recent instance, DELETEALL every
+    instance, SEARCH returns the least recent, SEARCHALL all in insertion order."""
+
+    def __init__(self):
+        self.S = []
+
+    def insert(self, k, v):
+        self.S.append((k, v))
+
+    def delete(self, k):
+        for i, (x, _) in enumerate(self.S):
+            if x == k:
+                del self.S[i]
+                return True
+        return False
+
+    def delete_all(self, k):
+        n = sum(1 for x, _ in self.S if x == k)
+        self.S = [(x, y) for x, y in self.S if x != k]
+        return n
+
+    def search_all(self, k):
+        return [y for x, y in self.S if x == k]
+
+
+def _multiset_table(B, lib, a=7, b=3):
+    t = OracleTable(B, a, b, lib=lib)
+    t.set_multiset()
+    return t
+
+
+def pin_multiset_golden(lib):
+    """Hand-derived INSERT / DELETE / DELETEALL / SEARCH(ALL) / FLUSH sequence on one
+    bucket (tests/golden/multiset_flush_example.txt)."""
+    t = _multiset_table(1, lib)
+    for row in _rows("multiset_flush_example.txt"):
+        op, args = row[0], row[1:]
+        want = args[args.index("->") + 1:] if "->" in args else None
+        args = args[: args.index("->")] if "->" in args else args
+        if op == "insert":
+            t.insert([int(args[0])], [int(args[1])])
+        elif op == "delete":
+            assert int(t.delete([int(args[0])])[0]) == int(want[0])
+        elif op == "delete_all":
+            assert int(t.delete_all([int(args[0])])[0]) == int(want[0])
+        elif op == "search":
+            v, f = t.search([int(args[0])])
+            assert f[0] == 1 and int(v[0]) == int(want[0])
+        elif op == "search_all":
+            c, vals = t.search_all([int(args[0])], 8)
+            assert vals[0, : int(c[0])].tolist() == [int(x) for x in want]
+        elif op == "export":
+            _, k, v = t.export()
+            assert [f"{a}:{b}" for a, b in zip(k.tolist(), v.tolist())] == want
+        elif op == "slabs":
+            assert t.stats()[2]["slabs"] == int(want[0])
+        elif op == "flush":
+            assert t.flush() == int(want[0])
+        else:
+            raise AssertionError(op)
+
+
+def pin_multiset_bruteforce(lib):
+    """Random INSERT / DELETE / DELETEALL / SEARCH(ALL) sequences over a tiny key
+    universe agree with the flat multiset model. Every instance of a key carries the
+    same value, so which instance a DELETE removes cannot show; the counts, found
+    flags and the live multiset must match exactly."""
+    rnd = random.Random(4321)
+    for trial in range(50):
+        B = 1 + trial % 3
+        t = _multiset_table(B, lib, rnd.randrange(1, P), rnd.randrange(0, P))
+        ref = FlatMultiset()
+        for _ in range(150):
+            op = rnd.randrange(5)
+            k = rnd.randrange(8) * 104729
+            v = k ^ 0x5A5A
+            if op <= 1:
+                t.insert([k], [v])
+                ref.insert(k, v)
+            elif op == 2:
+                assert int(t.delete([k])[0]) == int(ref.delete(k))
+            elif op == 3:
+                assert int(t.delete_all([k])[0]) == ref.delete_all(k)
+            else:
+                c, vals = t.search_all([k], 64)
+                want = ref.search_all(k)
+                assert int(c[0]) == len(want) and vals[0, : len(want)].tolist() == want
+                sv, sf = t.search([k])
+                assert int(sf[0]) == int(bool(want)) and (not want or int(sv[0]) == want[0])
+        _, _, tot = t.stats()
+        assert tot["live"] == len(ref.S)
+        _, kk, vv = t.export()
+        assert sorted(zip(kk.tolist(), vv.tolist())) == sorted(ref.S)
+
+
+def pin_multiset_insert_order(lib):
+    """With no deletes, list order is insertion order: SEARCH returns the least
+    recently inserted value and SEARCHALL returns them in insertion order
+    (Sec. 3.2 definitions); duplicates occupy one slot each (slots = inserts)."""
+    rng = np.random.default_rng(5)
+    t = _multiset_table(13, lib)
+    keys = rng.integers(0, 40, 2000).astype(np.uint32)
+    vals = np.arange(2000, dtype=np.uint32)
+    f = t.insert(keys, vals)
+    assert f.sum() == 0
+    v, found = t.search(np.arange(40, dtype=np.uint32))
+    c, allv = t.search_all(np.arange(40, dtype=np.uint32), 200)
+    for k in range(40):
+        idx = np.flatnonzero(keys == k)
+        assert int(c[k]) == len(idx)
+        if len(idx):
+            assert found[k] == 1 and int(v[k]) == int(idx[0])
+            assert allv[k, : min(len(idx), 200)].tolist() == idx[:200].tolist()
+    _, _, tot = t.stats()
+    assert tot["slots"] == 2000 and tot["live"] == 2000
+
+
+def pin_set_table_all_ops(lib):
+    """In a set table (unique keys) SEARCHALL finds at most one instance and agrees
+    with SEARCH, and DELETEALL does what DELETE does."""
+    rng = np.random.default_rng(6)
+    keys = rng.choice(1 << 24, 3000, replace=False).astype(np.uint32)
+    t1 = OracleTable(101, 9, 4, lib=lib)
+    t2 = OracleTable(101, 9, 4, lib=lib)
+    for t in (t1, t2):
+        t.insert(keys, keys + np.uint32(1))
+    q = np.concatenate([keys[:500], rng.choice(1 << 24, 500).astype(np.uint32) | np.uint32(1 << 25)])
+    c, vals = t1.search_all(q, 2)
+    v, f = t1.search(q)
+    assert (c == f).all() and (vals[f == 1, 0] == v[f == 1]).all()
+    d1 = t1.delete(keys[::4])
+    d2 = t2.delete_all(keys[::4])
+    assert (d1 == d2).all()
+    assert t1.stats()[2] == t2.stats()[2]
+    assert all((x == y).all() for x, y in zip(t1.export(), t2.export()))
+
+
+def pin_flush_compacts(lib):
+    """Sec. 4.3.4 FLUSH: the live elements (and their list order) are unchanged,
+    every bucket keeps the minimum number of slabs, max(1, ceil(live / M)), counted
+    here from the exported elements, and the released slabs are the difference.
+    The flushed table then behaves like a fresh one filled with the export in order."""
+    rng = np.random.default_rng(8)
+    for key_only, multiset in ((False, False), (True, False), (False, True)):
+        M = 30 if key_only else 15
+        B = 50
+        t = OracleTable(B, 3, 1, key_only=key_only, lib=lib)
+        if multiset:
+            t.set_multiset()
+        keys = rng.choice(1 << 24, 4000, replace=False).astype(np.uint32)
+        t.insert(keys, keys ^ np.uint32(3))
+        t.delete(keys[rng.permutation(4000)[:2500]])
+        before_export = t.export()
+        before_slabs = t.stats()[2]["slabs"]
+        released = t.flush()
+        after = t.export()
+        assert all((x == y).all() for x, y in zip(before_export, after))
+        live = np.bincount(after[0], minlength=B)
+        _, slabs, tot = t.stats()
+        assert (slabs == np.maximum(1, (live + M - 1) // M)).all()
+        assert tot["slots"] == len(after[0]) and released == before_slabs - tot["slabs"]
+        fresh = OracleTable(B, 3, 1, key_only=key_only, lib=lib)
+        if multiset:
+            fresh.set_multiset()
+        fresh.insert(after[1], after[2])
+        assert (fresh.stats()[1] == slabs).all() and (fresh.stats()[0] == t.stats()[0]).all()
+        more = rng.choice(1 << 24, 800, replace=False).astype(np.uint32) | np.uint32(1 << 25)
+        t.insert(more, more)
+        fresh.insert(more, more)
+        assert all((x == y).all() for x, y in zip(t.export(), fresh.export()))
+        assert t.flush() == 0 or not multiset
+
+
+def pin_flush_noop_and_empty(lib):
+    """FLUSH of a table without deletes changes nothing; FLUSH after deleting
+    everything leaves every bucket one empty slab."""
+    rng = np.random.default_rng(12)
+    keys = rng.choice(1 << 24, 1000, replace=False).astype(np.uint32)
+    t = OracleTable(20, 5, 6, lib=lib)
+    t.insert(keys, keys)
+    s0, b0, tot0 = t.stats()
+    assert t.flush() == 0
+    s1, b1, tot1 = t.stats()
+    assert (s0 == s1).all() and (b0 == b1).all() and tot0 == tot1
+    t.delete(keys)
+    released = t.flush()
+    s2, b2, tot2 = t.stats()
+    assert (s2 == 0).all() and (b2 == 1).all() and released == tot1["slabs"] - 20
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -22,7 +22,17 @@ MUTANTS = {
                        "(uint64_t)b * (uint64_t)key + (uint64_t)a"),
     "hash_wrong_prime": ("#define OR_PRIME 4294967291ull", "#define OR_PRIME 4294967279ull"),
     "hash_skips_mod_p": ("(x % OR_PRIME) % num_buckets", "x % num_buckets"),
-    "tombstone_matches": ("if (bk->s[s].live && bk->s[s].key == key)", "if (bk->s[s].key == key)"),
+    "tombstone_matches": ("if (bk->s[s].live == OR_LIVE && bk->s[s].key == key)", "if (bk->s[s].key == key)"),
+    "multiset_insert_appends": ("while (s < bk->len && bk->s[s].live != OR_HOLE) s++;", "s = bk->len;"),
+    "multiset_delete_tombstones": ("bk->s[s].live = t->multiset ? OR_HOLE : OR_TOMB;", "bk->s[s].live = OR_TOMB;"),
+    "delete_all_first_only": ("                    kill(t, bk, s);\n                    c++;\n",
+                              "                    kill(t, bk, s);\n                    c++;\n                    break;\n"),
+    "search_all_counts_twice": ("values[i * cap + c] = t->key_only ? 0u : bk->s[s].value;\n                c++;",
+                                "values[i * cap + c] = t->key_only ? 0u : bk->s[s].value;\n                c += 2;"),
+    "flush_keeps_tombstones": ("if (bk->s[s].live == OR_LIVE) bk->s[w++] = bk->s[s];",
+                               "if (bk->s[s].live != OR_HOLE) bk->s[w++] = bk->s[s];"),
+    "flush_reverses_order": ("if (bk->s[s].live == OR_LIVE) bk->s[w++] = bk->s[s];",
+                             "if (bk->s[s].live == OR_LIVE) { or_slot x = bk->s[s]; for (uint32_t q = w++; q > 0; q--) bk->s[q] = bk->s[q - 1]; bk->s[0] = x; }"),
     "slab_count_off_by_one": ("(len + t->M - 1) / t->M", "len / t->M + 1"),
     "wrong_pairs_per_slab": ("t->M = key_only ? 30u : 15u;", "t->M = key_only ? 30u : 16u;"),
     "search_lines_off_by_one": (
