@@ -93,6 +93,8 @@ typedef struct slab_info {
     uint32_t num_super_blocks;   /* ceil(num_memory_blocks / blocks_per_super) */
     uint32_t sm_count;
     uint64_t device_bytes;       /* bytes the table holds on the device */
+    int32_t multiset;            /* 1: duplicates allowed (slab_set_multiset) */
+    int32_t pad;
 } slab_info;
 
 /*
@@ -296,6 +298,55 @@ int slab_copy_bitmaps(const slab_table *t, uint32_t *d_dst, uint64_t n_words, vo
  */
 int slab_chain_histogram_noalloc(slab_table *t, uint32_t n_bins, uint64_t *h_hist, uint64_t *h_totals,
                                  void *stream);
+
+/*
+ * Multiset tables and the remaining operations of Sec. 3.2 / 4.3.4.
+ *
+ * slab_set_multiset: make a table that holds no keys (new, or after
+ * slab_reset) a multiset (on = 1) or a set again (on = 0). In a multiset
+ * table every insert (slab_insert_batch and the insert op of
+ * slab_mixed_batch) is Sec. 3.2 INSERT: the pair goes into the first empty
+ * slot of its list with no uniqueness check (found = 0, mixed result 1); a
+ * delete removes the first instance met walking the list and empties its
+ * slot, the whole pair at once, so later inserts reuse it (Sec. 3.2
+ * "Deletion"). Search returns the first instance met. Within one batch each
+ * key may appear in at most one op; a batch that both inserts and deletes in
+ * the same bucket may leave an emptied slot behind a newly linked slab.
+ * Not available for tables of a group. SLAB_ERR_INVALID_ARG if the table may
+ * hold keys.
+ *
+ * slab_search_all_batch: SEARCHALL (Sec. 3.2) of n keys. d_counts[i]
+ * receives how many live instances key i has; their values (0 in key-only
+ * mode) go to d_values_out[i * max_per_key + j] for j < min(count,
+ * max_per_key), in list order; the rest of the row is left as it was.
+ * d_values_out holds n * max_per_key uint32 (may be NULL when max_per_key is
+ * 0). Read-only: it may not share a batch window with writes to the table.
+ *
+ * slab_delete_all_batch: DELETEALL (Sec. 3.2): every live instance of each
+ * key is removed (tombstone in a set table, emptied slot in a multiset
+ * table); d_counts[i] (nullable) receives how many.
+ *
+ * slab_flush: FLUSH (Sec. 4.3.4) of every bucket, one warp per bucket: the
+ * live elements keep their list order and move to the front of the list,
+ * tombstones and emptied slots disappear, each list keeps max(1, ceil(live /
+ * M)) slabs and the rest are emptied and returned to SlabAlloc. Must not run
+ * concurrently with any other call on the table. *h_released (nullable; when
+ * given, the call synchronizes `stream`) receives the number of slabs freed.
+ *
+ * slab_grow_pool: add ceil(extra_slabs / 1024) memory blocks to the SlabAlloc
+ * pool (Sec. 5: more super blocks once the pool runs short). Existing slabs
+ * keep their addresses; the table moves to a larger allocation. Synchronous:
+ * waits for the device, and no other call may be in flight on the table.
+ * SLAB_ERR_INVALID_ARG for a table of a group, extra_slabs = 0, or a pool
+ * beyond the 32-bit address space; SLAB_ERR_CUDA if the allocation fails (the
+ * table is left as it was).
+ */
+int slab_set_multiset(slab_table *t, int on);
+int slab_search_all_batch(slab_table *t, const uint32_t *d_keys, uint32_t n, uint32_t max_per_key,
+                          uint32_t *d_counts, uint32_t *d_values_out, void *stream);
+int slab_delete_all_batch(slab_table *t, const uint32_t *d_keys, uint32_t *d_counts, uint32_t n, void *stream);
+int slab_flush(slab_table *t, uint64_t *h_released, void *stream);
+int slab_grow_pool(slab_table *t, uint64_t extra_slabs);
 
 /*
  * Groups: many independent slab hashes served by one persistent launch (a library

@@ -128,7 +128,7 @@ __global__ void __maxnreg__(SLAB_GROUP_MAXNREG)
         stage_slabs(T, buf_s, cb, __ballot_sync(kFull, walk), lane);
         cp_async_commit();
         cp_async_wait<0>();
-        skeys[lane] = ck;
+        skeys[lane] = match_key(T, ck, co);
         if constexpr (kKind == kKindMixed) salts[lane] = alt_key(ck, co);
         __syncwarp();
         serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb, idx,

@@ -41,6 +41,7 @@ struct TableView {
     uint32_t epoch;       // distinct per launch; spreads resident blocks over launches
     uint32_t prefetch_l2; // staged kernels pull the next tile's base slabs into L2 (tables much larger than L2)
     uint32_t learned;     // 1: buckets come from the learned model, 0: from the universal hash
+    uint32_t multiset;    // 1: duplicates allowed (INSERT, deletes empty their slot), 0: set (REPLACE, tombstones)
 };
 
 struct BatchArgs {
@@ -109,6 +110,26 @@ __device__ __forceinline__ uint32_t ld_slab(const uint32_t* p) {
 
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed64(uint32_t* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Remove the element whose key sits at word d of the slab at p (Sec. 3.2
+// "Deletion"): a set table marks it deleted (the tombstone keeps later replaces
+// from re-inserting a key further down the list); a multiset table empties it,
+// the whole pair in one store, so a later insert can claim the slot.
+template <bool kKeyOnly>
+__device__ __forceinline__ void remove_at(const TableView& T, uint32_t* p, uint32_t d) {
+    if (!T.multiset) st_relaxed(p + d, kTombstone);
+    else if (kKeyOnly) st_relaxed(p + d, kEmptyKey);
+    else st_relaxed64(p + d, ~0ull);
+}
+
+// The key an op's WCWS step matches: a multiset insert looks for an empty slot
+// only (no uniqueness check, Sec. 3.2 INSERT); every other op for its own key.
+__device__ __forceinline__ uint32_t match_key(const TableView& T, uint32_t key, uint32_t op) {
+    return T.multiset && op == kOpInsert ? kEmptyKey : key;
 }
 
 // Streaming loads for the op arrays: each element is read once, so mark it

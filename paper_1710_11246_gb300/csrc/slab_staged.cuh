@@ -168,12 +168,12 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                     fnd = 1u;
                     pending = false;
                 } else if (myop == kOpDelete) {
-                    st_relaxed(gslab + d, kTombstone);
+                    remove_at<kKeyOnly>(T, gslab, d);
                     res = 1u;
                     fnd = 1u;
                     pending = false;
                 } else if constexpr (kKeyOnly) {
-                    if (buf[swz(lane, d)] == ck) {  // already present
+                    if (!T.multiset && buf[swz(lane, d)] == ck) {  // already present
                         res = 0u;
                         fnd = 1u;
                         pending = false;
@@ -220,7 +220,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                     pending = false;
                     break;
                 }
-                if (!cas_new || (uint32_t)cas_got == ck || d + kPairStride > kLastKeyLane) break;
+                if (!cas_new || ((uint32_t)cas_got == ck && !T.multiset) || d + kPairStride > kLastKeyLane) break;
                 d += kPairStride;
                 if constexpr (kKeyOnly) {
                     cas_got = atomicCAS(gslab + d, kEmptyKey, ck);
@@ -337,7 +337,7 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
         if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kWordsPerSlab);
         uint32_t mk, mv, mo;
         fetch(t + 2u * nwarps, mk, mv, mo);
-        skeys[lane] = ck;  // the WCWS steps read keys four at a time from here
+        skeys[lane] = match_key(T, ck, co);  // the WCWS steps read keys four at a time from here
         if constexpr (kKind == kKindMixed) salts[lane] = alt_key(ck, co);
         // (3) serve this tile once its slabs have landed
         cp_async_wait<0>();

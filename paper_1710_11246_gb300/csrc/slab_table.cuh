@@ -31,6 +31,7 @@ struct slab_table {
     bool model_fitted = false;
     bool dirty = false;               // a batch may have stored keys since create / reset
     bool owns_memory = true;          // false for a table that lives inside a slab_group's arena
+    bool multiset = false;            // duplicates allowed (INSERT), deletes empty their slot
 };
 
 namespace slab_host {
@@ -57,6 +58,7 @@ inline slab::TableView view(slab_table* t) {
     v.epoch = ++t->epoch;
     v.prefetch_l2 = (uint64_t)t->num_buckets * 128ull > (uint64_t)t->l2_bytes / 2;
     v.learned = t->learned ? 1u : 0u;
+    v.multiset = t->multiset ? 1u : 0u;
     return v;
 }
 

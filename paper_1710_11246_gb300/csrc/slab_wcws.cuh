@@ -25,11 +25,13 @@ struct Outcome {
 // lane. Ballots find a matching key (or, for insert, the first empty-or-matching
 // pair); a miss hands over the address lane's next pointer.
 template <bool kKeyOnly>
-__device__ __forceinline__ Outcome examine(uint32_t data, uint32_t sop, uint32_t skey) {
+__device__ __forceinline__ Outcome examine(uint32_t data, uint32_t sop, uint32_t skey, bool multiset) {
     constexpr uint32_t kMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
     Outcome o;
     if (sop == kOpInsert) {
-        uint32_t m = __ballot_sync(kFull, data == kEmptyKey || data == skey) & kMask;
+        // REPLACE looks for the key or the first empty pair; a multiset INSERT
+        // for the first empty pair only (Sec. 3.2)
+        uint32_t m = __ballot_sync(kFull, data == kEmptyKey || (!multiset && data == skey)) & kMask;
         if (m) {
             int d = __ffs(m) - 1;
             uint32_t ok = __shfl_sync(kFull, data, d);
@@ -139,7 +141,7 @@ __global__ void direct_kernel(TableView T, BatchArgs A) {
                     active = false;
                 }
             } else {
-                const Outcome o = examine<kKeyOnly>(data, sop, skey);
+                const Outcome o = examine<kKeyOnly>(data, sop, skey, T.multiset != 0);
                 if (o.kind == kResolved) {
                     if ((int)lane == s) { res = o.a; fnd = o.b; active = false; }
                 } else if (o.kind == kAdvance) {
@@ -151,7 +153,7 @@ __global__ void direct_kernel(TableView T, BatchArgs A) {
                     }
                 } else if (o.kind == kMarkDead) {
                     if ((int)lane == s) {
-                        st_relaxed(p + o.a, kTombstone);
+                        remove_at<kKeyOnly>(T, p, o.a);
                         res = 1u; fnd = 1u; active = false;
                     }
                 } else if (o.kind == kClaim) {

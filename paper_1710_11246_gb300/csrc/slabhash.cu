@@ -407,6 +407,8 @@ int slab_get_info(const slab_table* t, slab_info* out) {
     out->num_super_blocks = (t->num_blocks + kBlocksPerSuper - 1) / kBlocksPerSuper;
     out->sm_count = (uint32_t)t->sm_count;
     out->device_bytes = t->device_bytes;
+    out->multiset = t->multiset ? 1 : 0;
+    out->pad = 0;
     return SLAB_OK;
 }
 

@@ -36,6 +36,7 @@ EXPORTED = [
     "slab_group_status",
     "slab_server_create", "slab_server_destroy", "slab_server_submit", "slab_server_collect",
     "slab_server_get_stats", "slab_server_run",
+    "slab_set_multiset", "slab_search_all_batch", "slab_delete_all_batch", "slab_flush", "slab_grow_pool",
 ]
 SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY = 64, 1 << 24, 1
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
@@ -51,7 +52,8 @@ class SlabInfo(C.Structure):
     _fields_ = [("num_buckets", C.c_uint32), ("mode", C.c_int32), ("elements_per_slab", C.c_uint32),
                 ("hash_a", C.c_uint32), ("hash_b", C.c_uint32), ("pool_slabs", C.c_uint64),
                 ("num_memory_blocks", C.c_uint32), ("blocks_per_super", C.c_uint32),
-                ("num_super_blocks", C.c_uint32), ("sm_count", C.c_uint32), ("device_bytes", C.c_uint64)]
+                ("num_super_blocks", C.c_uint32), ("sm_count", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("multiset", C.c_int32), ("pad", C.c_int32)]
 
 
 class SlabLearnReport(C.Structure):
@@ -125,6 +127,11 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_group_search": (i32, [vp, vp, vp, vp, vp, u32, vp]),
             "slab_group_mixed": (i32, [vp, vp, vp, vp, vp, vp, vp, u32, vp]),
             "slab_group_status": (i32, [vp, vp, C.POINTER(u32)]),
+            "slab_set_multiset": (i32, [vp, i32]),
+            "slab_search_all_batch": (i32, [vp, vp, u32, u32, vp, vp, vp]),
+            "slab_delete_all_batch": (i32, [vp, vp, vp, u32, vp]),
+            "slab_flush": (i32, [vp, C.POINTER(u64), vp]),
+            "slab_grow_pool": (i32, [vp, u64]),
             "slab_server_create": (i32, [vp, u32, u32, C.c_double, u32, C.POINTER(vp)]),
             "slab_server_destroy": (None, [vp]),
             "slab_server_submit": (i32, [vp, vp, vp, vp, u32, C.POINTER(u64)]),
@@ -414,6 +421,38 @@ def slab_group_status(g: int, stream=None) -> tuple[int, int]:
     if rc == SLAB_ERR_CUDA or rc == SLAB_ERR_INVALID_ARG:
         raise SlabError(rc, "slab_group_status")
     return rc, flags.value
+
+
+# ------------------------------------------------------------------ paper variants
+def slab_set_multiset(t: int, on: bool = True) -> None:
+    _check(load_library().slab_set_multiset(t, int(bool(on))), "slab_set_multiset")
+
+
+def slab_search_all_batch(t: int, keys, max_per_key: int, counts, values_out=None, n: int | None = None,
+                          stream=None) -> None:
+    n = keys.numel() if n is None else n
+    _check(load_library().slab_search_all_batch(
+        t, _dptr(keys, 4, n, "keys"), n, max_per_key, _dptr(counts, 4, n, "counts"),
+        _dptr(values_out, 4, n * max_per_key, "values_out", nullable=max_per_key == 0), _stream(stream)),
+        "slab_search_all_batch")
+
+
+def slab_delete_all_batch(t: int, keys, counts=None, n: int | None = None, stream=None) -> None:
+    n = keys.numel() if n is None else n
+    _check(load_library().slab_delete_all_batch(t, _dptr(keys, 4, n, "keys"),
+                                                _dptr(counts, 4, n, "counts", nullable=True), n, _stream(stream)),
+           "slab_delete_all_batch")
+
+
+def slab_flush(t: int, stream=None, wait: bool = True):
+    """Compact every bucket (Sec. 4.3.4); returns the slabs released when wait is set."""
+    r = C.c_uint64(0)
+    _check(load_library().slab_flush(t, C.byref(r) if wait else None, _stream(stream)), "slab_flush")
+    return r.value if wait else None
+
+
+def slab_grow_pool(t: int, extra_slabs: int) -> None:
+    _check(load_library().slab_grow_pool(t, extra_slabs), "slab_grow_pool")
 
 
 # ------------------------------------------------------------------ serving

@@ -77,18 +77,24 @@ class Pair:
         assert (rg == ro).all(), f"mixed results: {np.flatnonzero(rg != ro)[:10]}"
         return ro, fo
 
-    def check_structure(self, expect_flags=0):
+    def check_structure(self, expect_flags=0, allow_holes=False, slabs_fixed=True):
         """Per-bucket used slots and slab counts, live multiset, bucket membership,
-        allocator bitmaps and status all agree with the oracle / invariants."""
+        allocator bitmaps and status all agree with the oracle / invariants.
+        allow_holes: multiset tables after deletes (used slots need not be a
+        prefix of the list); slabs_fixed=False skips the per-bucket slab counts
+        (a multiset batch mixing inserts and deletes does not fix them)."""
         rc, flags = self.g.status()
         assert flags == expect_flags, (rc, flags)
         slots, slabs, tot = self.g.stats(per_bucket=True)
         oslots, oslabs, otot = self.o.stats()
         gs, gb = host(slots), host(slabs)
         assert (gs == oslots).all(), f"slots differ in buckets {np.flatnonzero(gs != oslots)[:10]}"
-        assert (gb == oslabs).all(), f"slabs differ in buckets {np.flatnonzero(gb != oslabs)[:10]}"
-        assert tot["live"] == otot["live"] and tot["slots"] == otot["slots"] and tot["slabs"] == otot["slabs"]
-        assert tot["prefix_violations"] == 0
+        assert tot["live"] == otot["live"] and tot["slots"] == otot["slots"]
+        if slabs_fixed:
+            assert (gb == oslabs).all(), f"slabs differ in buckets {np.flatnonzero(gb != oslabs)[:10]}"
+            assert tot["slabs"] == otot["slabs"]
+        if not allow_holes:
+            assert tot["prefix_violations"] == 0
         assert tot["pool_allocated"] == tot["linked"], "allocated slabs must all be linked"
         b, k, v = self.g.export()
         ob, ok, ov = self.o.export()
