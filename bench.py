@@ -45,8 +45,8 @@ PHASES = ("reset", "build", "search", "delete", "mixed")
 # They describe the kernel sources they were taken from and are dropped as soon as
 # those sources change.
 KERNEL_SOURCES = ("slab_device.cuh", "slab_wcws.cuh", "slab_staged.cuh", "slabhash.cu")
-NCU_TRAFFIC = {"sources_sha256": "88744b4d2df8458e",
-               "build": 103.61e6, "search": 99.29e6, "delete": 60.83e6, "mixed": 66.78e6}
+NCU_TRAFFIC = {"sources_sha256": "f12e0d681203a719",
+               "build": 103.52e6, "search": 99.57e6, "delete": 60.94e6, "mixed": 66.72e6}
 
 
 def ncu_traffic(phase: str):
@@ -453,6 +453,8 @@ def sweep(args, device):
         group_sweep(args, device, stream, flush)
     if want("serving"):
         serving_sweep(args, device, stream, flush)
+    if want("flush"):
+        flush_sweep(args, device, stream, flush)
     if not want("mixed"):
         return
     # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
@@ -695,6 +697,60 @@ def serving_sweep(args, device, stream, flush):
     t.close()
 
 
+def flush_sweep(args, device, stream, flush):
+    """FLUSH (Sec. 4.3.4) after tombstones pile up: preload 2^22 pairs (beta 0.6),
+    churn with 32 mixed batches of 2^20 ops at (0.5, 0.5, 0) (every delete leaves a
+    tombstone, every insert takes a new slot), then time search (2^22 at 50 % hit)
+    and one more churn batch before and after one flush of the whole table."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
+    w = W.config2(BETA, HIT, args.seed)
+    ks = W.KeyStream(args.seed)
+    ks.take(N_KEYS + N_SEARCH)
+    rng = np.random.default_rng([args.seed, 0xF1])
+    t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 22)
+    h = t.handle
+    with torch.cuda.stream(stream):
+        sh.slab_insert_batch(h, dev(w.keys), dev(w.values), None, stream=stream)
+    live = w.keys
+    res = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+    churn_ms = []
+    for _ in range(33):
+        mb, live = W.mixed_batch(ks, live, N_MIXED, (0.5, 0.5, 0.0), rng)
+        o, k, v = torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)
+        churn_ms.append(_time_ms(lambda: sh.slab_mixed_batch(h, o, k, v, res, None, stream=stream), stream, flush))
+    # search keys: half live, half absent
+    q = np.concatenate([live[rng.permutation(len(live))[: N_SEARCH // 2]], ks.take(N_SEARCH // 2)])
+    dq = dev(q[rng.permutation(N_SEARCH)])
+    out = torch.empty(N_SEARCH, dtype=torch.int32, device=device)
+    search_before = min(_time_ms(lambda: sh.slab_search_batch(h, dq, out, None, stream=stream), stream, flush)
+                        for _ in range(3))
+    before = t.stats()
+    flush_ms = _time_ms(lambda: sh.slab_flush(h, stream, wait=False), stream, flush)
+    after = t.stats()
+    search_after = min(_time_ms(lambda: sh.slab_search_batch(h, dq, out, None, stream=stream), stream, flush)
+                       for _ in range(3))
+    mb, live = W.mixed_batch(ks, live, N_MIXED, (0.5, 0.5, 0.0), rng)
+    o, k, v = torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)
+    churn_after = _time_ms(lambda: sh.slab_mixed_batch(h, o, k, v, res, None, stream=stream), stream, flush)
+    rc, _ = t.status(stream)
+    line = {"sweep": "flush", "keys": N_KEYS, "num_buckets": w.num_buckets, "churn_batches": 32,
+            "churn_ops": N_MIXED, "unit": "Mops/s",
+            "slabs_per_bucket_before": round(before["slabs"] / w.num_buckets, 3),
+            "slabs_per_bucket_after": round(after["slabs"] / w.num_buckets, 3),
+            "slabs_released": before["slabs"] - after["slabs"], "live": after["live"],
+            "flush_ms": round(flush_ms, 3), "flush_buckets_per_s": round(w.num_buckets / (flush_ms * 1e-3)),
+            "search_50_before": round(N_SEARCH / (search_before * 1e3), 1),
+            "search_50_after": round(N_SEARCH / (search_after * 1e3), 1),
+            "churn_first_batch": round(N_MIXED / (churn_ms[0] * 1e3), 1),
+            "churn_batch_before_flush": round(N_MIXED / (churn_ms[-1] * 1e3), 1),
+            "churn_batch_after_flush": round(N_MIXED / (churn_after * 1e3), 1), "status": rc}
+    print(json.dumps(line), flush=True)
+    t.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -708,7 +764,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--sweep", nargs="?", const="all", default=None,
-                    choices=["all", "bulk", "slaballoc", "learned", "group", "serving", "mixed"],
+                    choices=["all", "bulk", "slaballoc", "learned", "group", "serving", "flush", "mixed"],
                     help="print the sweep lines (all, or one section) instead of the step line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
