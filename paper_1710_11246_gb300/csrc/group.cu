@@ -39,6 +39,7 @@ struct slab_group {
     std::vector<slab_table*> tables;  // non-owning handles into the arena
     slab_config cfg{};
     uint32_t epoch = 0;
+    int occupancy[4] = {};            // resident blocks per SM by kernel kind for cfg; 0 = not yet asked
 };
 
 namespace {
@@ -185,8 +186,12 @@ int launch_group(slab_group* g, const uint32_t* d_op_start, const BatchArgs& a, 
     if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SLAB_ERR_CUDA;
     int bps = g->cfg.blocks_per_sm;
-    if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, tpb, smem) != cudaSuccess)
-        return SLAB_ERR_CUDA;
+    if (bps == 0) {  // asked once per configuration: the query costs microseconds
+        int& occ = g->occupancy[kKind];
+        if (!occ && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, tpb, smem) != cudaSuccess)
+            return SLAB_ERR_CUDA;
+        bps = occ;
+    }
     tile_prefix_kernel<<<1, 1024, 0, S(stream)>>>(d_op_start, g->ntables, g->d_tile_start);
     const uint32_t grid = (uint32_t)std::max(1, std::max(bps, 1) * g->sm_count);
     k<<<grid, tpb, smem, S(stream)>>>(g->d_views, d_op_start, g->d_tile_start, g->ntables, ++g->epoch, a);
@@ -353,6 +358,8 @@ int slab_group_set_config(slab_group* g, const slab_config* c) {
         (uint64_t)(c->threads_per_block / 32) * kGroupWordsPerWarp * 4 > 227 * 1024 ||
         c->threads_per_block > group_block_limit(g->mode))
         return SLAB_ERR_INVALID_ARG;
+    if (c->threads_per_block != g->cfg.threads_per_block)
+        for (int& o : g->occupancy) o = 0;
     g->cfg = *c;
     g->cfg.variant = SLAB_VARIANT_STAGED;
     std::vector<TableView> views(g->ntables);

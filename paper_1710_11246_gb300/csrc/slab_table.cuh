@@ -32,6 +32,7 @@ struct slab_table {
     bool dirty = false;               // a batch may have stored keys since create / reset
     bool owns_memory = true;          // false for a table that lives inside a slab_group's arena
     bool multiset = false;            // duplicates allowed (INSERT), deletes empty their slot
+    int occupancy[2][4] = {};         // resident blocks per SM by [variant][kernel kind] for cfg; 0 = not yet asked
 };
 
 namespace slab_host {

@@ -241,8 +241,12 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
     if (t->cfg.variant == SLAB_VARIANT_DIRECT) {
         auto k = direct_kernel<kKind, kKeyOnly>;
         int bps = t->cfg.blocks_per_sm;
-        if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, tpb, 0) != cudaSuccess)
-            return SLAB_ERR_CUDA;
+        if (bps == 0) {  // the occupancy query costs microseconds: ask once per configuration
+            int& occ = t->occupancy[SLAB_VARIANT_DIRECT][kKind];
+            if (!occ && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, tpb, 0) != cudaSuccess)
+                return SLAB_ERR_CUDA;
+            bps = occ;
+        }
         const uint64_t tiles = (a.n + 31u) / 32u;
         const uint64_t want = (tiles + wpb - 1) / wpb;
         const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
@@ -255,8 +259,12 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return SLAB_ERR_CUDA;
         int bps = t->cfg.blocks_per_sm;
-        if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, tpb, smem) != cudaSuccess)
-            return SLAB_ERR_CUDA;
+        if (bps == 0) {
+            int& occ = t->occupancy[SLAB_VARIANT_STAGED][kKind];
+            if (!occ && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, tpb, smem) != cudaSuccess)
+                return SLAB_ERR_CUDA;
+            bps = occ;
+        }
         const uint64_t tiles = (a.n + 31u) / 32u;
         const uint64_t want = (tiles + wpb - 1) / wpb;
         const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
@@ -422,6 +430,9 @@ int slab_set_config(slab_table* t, const slab_config* cfg) {
     if (!t || !cfg || !valid_config(*cfg)) return SLAB_ERR_INVALID_ARG;
     if (cfg->variant == SLAB_VARIANT_STAGED && cfg->threads_per_block > staged_block_limit(t->mode))
         return SLAB_ERR_INVALID_ARG;
+    if (cfg->threads_per_block != t->cfg.threads_per_block)
+        for (auto& v : t->occupancy)
+            for (int& o : v) o = 0;
     t->cfg = *cfg;
     return SLAB_OK;
 }
