@@ -102,6 +102,29 @@ def run_oracle_step(w, mb):
     return time.perf_counter() - t0, lines
 
 
+def host_cpu() -> str:
+    """CPU model and logical core count of this host (best effort)."""
+    model = ""
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return f"{model or 'unknown CPU'}, {os.cpu_count()} logical cores"
+
+
 def cpu_baseline(w, mb, budget_s: float = 10.0):
     """The oracle as it stands, single-threaded, on whole steps of the same workload."""
     times, lines = [], None
@@ -110,7 +133,7 @@ def cpu_baseline(w, mb, budget_s: float = 10.0):
         dt, lines = run_oracle_step(w, mb)
         times.append(dt)
     v = OPS_PER_STEP * len(times) / sum(times) / 1e6
-    return {"value": round(v, 3), "unit": "Mops/s", "cores": 1, "kind": "oracle",
+    return {"value": round(v, 3), "unit": "Mops/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"{len(times)} whole step(s) of the workload ({OPS_PER_STEP} ops each), "
                       f"plain C oracle, one thread"}, lines, times
 
@@ -577,16 +600,39 @@ def slaballoc_sweep(device, stream, flush, reps):
     n = 1 << 24
     t = sh.SlabHash(8, 3, 4, 1 << 25)
     addrs = torch.empty(n, dtype=torch.int32, device=device)
-    a_ms, f_ms = [], []
+    a_ms, f_ms, a1_ms = [], [], []
     for _ in range(reps):
         with torch.cuda.stream(stream):
             sh.slab_reset(t.handle, stream)
         a_ms.append(_time_ms(lambda: sh.slab_alloc_batch(t.handle, addrs, stream=stream), stream, flush))
         f_ms.append(_time_ms(lambda: sh.slab_free_batch(t.handle, addrs, stream=stream), stream, flush))
+    # the paper's warp serves its requests one at a time (direct variant)
+    t.configure(variant=sh.SLAB_VARIANT_DIRECT)
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            sh.slab_reset(t.handle, stream)
+        a1_ms.append(_time_ms(lambda: sh.slab_alloc_batch(t.handle, addrs, stream=stream), stream, flush))
+        sh.slab_free_batch(t.handle, addrs, stream=stream)
+    t.configure(variant=sh.SLAB_VARIANT_STAGED)
     rc, flags = t.status(stream)
     bm_zero = bool((t.bitmaps() == 0).all().item())
+    # allocator ceiling: random 32-bit atomicOr on a bitmap region of the same size
+    words = (1 << 25) // 32
+    bm = torch.zeros(words, dtype=torch.int32, device=device)
+    or_rate = 0.0
+    for oif in (2, 4, 8):
+        ms = []
+        for rep in range(3):
+            bm.zero_()
+            ms.append(_time_ms(lambda: sh.slab_probe_random_or(bm, words, n, rep + 1, oif, 512, stream=stream),
+                               stream, flush))
+        or_rate = max(or_rate, n / (min(ms) * 1e-3))
+    del bm
     print(json.dumps({"sweep": "slaballoc", "allocations": n, "pool_slabs": 1 << 25, "unit": "Mops/s",
                       "alloc": round(n / (min(a_ms) * 1e3), 1), "free": round(n / (min(f_ms) * 1e3), 1),
+                      "alloc_one_at_a_time": round(n / (min(a1_ms) * 1e3), 1),
+                      "random_atomic_or_bitmap": round(or_rate / 1e6, 1),
+                      "alloc_frac_of_atomic_rate": round(n / (min(a_ms) * 1e-3) / or_rate, 4),
                       "status": rc, "bitmaps_clear_after_free": bm_zero}), flush=True)
     t.close()
     del addrs
@@ -946,7 +992,7 @@ def reference_arm(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "config": config_dict(),
-           "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 3), "unit": "Mops/s",
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "host": host_cpu(), "value": round(value, 3), "unit": "Mops/s",
                             "sample": f"whole steps ({OPS_PER_STEP} ops each), plain C oracle, one thread"},
            "e2e": {"value": round(value, 3), "unit": "Mops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

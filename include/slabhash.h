@@ -114,6 +114,14 @@ typedef struct slab_info {
 int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b,
                 uint64_t pool_slabs, slab_table **out);
 
+/* The universal hash parameters drawn from a seed (Sec. 3.3 "a, b random"):
+ * with x1, x2 the first two outputs of SplitMix64 seeded with `seed`,
+ * a = 1 + x1 mod (p - 1) and b = x2 mod p. Host only; SLAB_ERR_INVALID_ARG for
+ * NULL outputs. slab_create_seeded = slab_hash_params + slab_create; the drawn
+ * parameters are reported by slab_get_info. */
+int slab_hash_params(uint64_t seed, uint32_t *hash_a, uint32_t *hash_b);
+int slab_create_seeded(uint32_t num_buckets, int mode, uint64_t seed, uint64_t pool_slabs, slab_table **out);
+
 /* Free the table's device memory. Waits for the device first. NULL is a no-op. */
 void slab_destroy(slab_table *t);
 
@@ -254,10 +262,12 @@ int slab_bucket_of(slab_table *t, const uint32_t *d_keys, uint32_t *d_buckets_ou
 
 /*
  * SlabAlloc allocation microbenchmark (Sec. 5: one 128-byte slab allocation
- * per thread). n requests, one per lane; each warp serves its lanes' requests
- * one at a time with warp_allocate (ballot over the resident block's register
- * bitmaps, one atomic on the owning bitmap word, resident change by hash when
- * full). d_addrs_out: n uint32 slab addresses (unit bits [0,10), memory block
+ * per thread). n requests, one per lane. With SLAB_VARIANT_DIRECT each warp
+ * serves its lanes' requests one at a time as in the paper (ballot over the
+ * resident block's register bitmaps, one atomic on the owning bitmap word,
+ * resident change by hash when full); with SLAB_VARIANT_STAGED (the default)
+ * the k-th lane holding a free bit claims it for the k-th requesting lane, so a
+ * warp's 32 requests take one atomic round trip instead of 32. d_addrs_out: n uint32 slab addresses (unit bits [0,10), memory block
  * [10,24), super block [24,32)), or SLAB_EMPTY_KEY where the pool was
  * exhausted (and SLAB_FLAG_OUT_OF_SLABS set). The slabs are not linked into
  * any list; free them with slab_free_batch or slab_reset.
@@ -506,6 +516,11 @@ int slab_probe_random_lines(const uint32_t *d_buf, uint64_t footprint_lines, uin
                             uint32_t *d_sink, void *stream);
 int slab_probe_random_cas(unsigned long long *d_buf, uint64_t footprint_lines, uint64_t n_ops,
                           uint32_t seed, int ops_in_flight, int threads_per_block, void *stream);
+/* slab_probe_random_or: n_ops 32-bit atomicOr operations, each setting one random
+ * bit of a random word in [0, footprint_words) of d_buf, `ops_in_flight` per
+ * thread: the atomic a SlabAlloc claim issues on its bitmap word (Sec. 5). */
+int slab_probe_random_or(uint32_t *d_buf, uint64_t footprint_words, uint64_t n_ops, uint32_t seed,
+                         int ops_in_flight, int threads_per_block, void *stream);
 
 #ifdef __cplusplus
 }

@@ -85,6 +85,27 @@ __global__ void probe_cas_kernel(unsigned long long* buf, uint64_t footprint, ui
     }
 }
 
+template <int L>
+__global__ void probe_or_kernel(uint32_t* buf, uint64_t footprint, uint64_t n_ops, uint32_t seed) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t per = (n_ops + nthreads - 1) / nthreads;
+    const uint64_t begin = tid * per;
+    const uint64_t end = min(begin + per, n_ops);
+    for (uint64_t i = begin; i < end; i += L) {
+        uint32_t got[L];
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            const uint64_t r = i + j;
+            got[j] = r < end ? atomicOr(buf + pick(r, seed, footprint), 1u << (mix(r + 0xB17) & 31u)) : 0u;
+        }
+        uint32_t x = 0;
+#pragma unroll
+        for (int j = 0; j < L; ++j) x ^= got[j];
+        if (x == 0x5A5A5A5Au) buf[0] |= 1u;  // keeps the results live; practically never taken
+    }
+}
+
 int occupancy_grid(const void* fn, int tpb) {
     int dev = 0, sms = 0, bps = 0;
     cudaGetDevice(&dev);
@@ -129,6 +150,27 @@ int slab_probe_random_cas(unsigned long long* d_buf, uint64_t footprint_lines, u
     case L: {                                                                                             \
         const int g = occupancy_grid((const void*)probe_cas_kernel<L>, tpb);                              \
         probe_cas_kernel<L><<<g, tpb, 0, s>>>(d_buf, footprint_lines, n_ops, seed);                       \
+        break;                                                                                            \
+    }
+    switch (ops_in_flight) {
+        LAUNCH(1) LAUNCH(2) LAUNCH(4) LAUNCH(8)
+        default: return SLAB_ERR_INVALID_ARG;
+    }
+#undef LAUNCH
+    return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ERR_CUDA;
+}
+
+int slab_probe_random_or(uint32_t* d_buf, uint64_t footprint_words, uint64_t n_ops, uint32_t seed,
+                         int ops_in_flight, int threads_per_block, void* stream) {
+    if (!d_buf || footprint_words == 0 || footprint_words >= (1ull << 32) || threads_per_block < 32 ||
+        threads_per_block > 1024 || threads_per_block % 32)
+        return SLAB_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int tpb = threads_per_block;
+#define LAUNCH(L)                                                                                         \
+    case L: {                                                                                             \
+        const int g = occupancy_grid((const void*)probe_or_kernel<L>, tpb);                               \
+        probe_or_kernel<L><<<g, tpb, 0, s>>>(d_buf, footprint_words, n_ops, seed);                        \
         break;                                                                                            \
     }
     switch (ops_in_flight) {

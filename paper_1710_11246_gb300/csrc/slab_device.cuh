@@ -223,6 +223,53 @@ __device__ __forceinline__ uint32_t warp_allocate(const TableView& T, AllocCtx& 
     }
 }
 
+// Batched allocation: every lane with `want` set receives its own pool address (or
+// kAllocFailed once every block has been probed). Lane i owns word i of the
+// resident block's bitmap, so in one round the k-th lane holding a free bit
+// claims it for the k-th requesting lane (lane order), and up to 32 claims are
+// in flight together instead of one per round trip. Losers of a bit race (the
+// atomic found the bit already set) refresh their word and go round again.
+// Must be called by all 32 lanes with warp-uniform control flow.
+__device__ __forceinline__ uint32_t warp_allocate_many(const TableView& T, AllocCtx& c, uint32_t warp_gid,
+                                                       bool want) {
+    const uint32_t lane = lane_id();
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t max_changes = T.random_probes + T.num_blocks;
+    uint32_t got = kAllocFailed;
+    for (uint32_t pending = __ballot_sync(kFull, want); pending;) {
+        if (c.block == kNoBlock) {
+            if (c.changes >= max_changes) break;
+            c.block = resident_block(T, warp_gid, c.changes);
+            c.changes++;
+            c.bitmap = ld_coherent(T.bitmaps + (uint64_t)c.block * 32 + lane);
+        }
+        const uint32_t free_lanes = __ballot_sync(kFull, c.bitmap != 0xFFFFFFFFu);
+        if (free_lanes == 0) {
+            c.block = kNoBlock;
+            continue;
+        }
+        const uint32_t serve = min(__popc(free_lanes), __popc(pending));
+        uint32_t addr = 0, ok = 0;
+        if (((free_lanes >> lane) & 1u) && (uint32_t)__popc(free_lanes & below) < serve) {
+            const uint32_t bit = (uint32_t)(__ffs(~c.bitmap) - 1);
+            const uint32_t mask = 1u << bit;
+            const uint32_t old = atomicOr(T.bitmaps + (uint64_t)c.block * 32 + lane, mask);
+            c.bitmap = old | mask;  // refresh from what the atomic saw
+            ok = (old & mask) == 0;
+            addr = (c.block << 10) | (lane << 5) | bit;
+        }
+        // requester of rank r takes the result of the r-th free lane
+        const uint32_t rank = __popc(pending & below);
+        const bool mine = ((pending >> lane) & 1u) && rank < serve;
+        const int src = mine ? (int)__fns(free_lanes, 0, (int)rank + 1) : (int)lane;
+        const uint32_t a = __shfl_sync(kFull, addr, src);
+        const uint32_t o = __shfl_sync(kFull, ok, src);
+        if (mine && o) got = a;
+        pending = __ballot_sync(kFull, want && got == kAllocFailed);
+    }
+    return got;
+}
+
 // Deallocation (Sec. 5): clear the unit's bit in its memory block's bitmap.
 __device__ __forceinline__ void deallocate(const TableView& T, uint32_t addr) {
     uint32_t block = addr >> 10, word = (addr >> 5) & 31u, bit = addr & 31u;

@@ -87,6 +87,22 @@ __device__ __forceinline__ uint32_t grow_list(const TableView& T, AllocCtx& ac, 
     return old;
 }
 
+// Warp-wide, batched: every lane with `need` set links one new slab behind its
+// own full slab at `p` (the slab its op last read). The slabs for all such lanes
+// come from one batched allocation; each lane then issues its own 32-bit link
+// CAS on its slab's next pointer, and a lane that loses (another op linked first)
+// returns its slab and follows the winner's. Returns the slab to continue with,
+// or kAllocFailed where the pool had no slab left.
+__device__ __forceinline__ uint32_t grow_lists(const TableView& T, AllocCtx& ac, uint32_t warp_gid, uint32_t* p,
+                                               bool need) {
+    const uint32_t na = warp_allocate_many(T, ac, warp_gid, need);
+    if (!need || na == kAllocFailed) return kAllocFailed;
+    const uint32_t old = atomicCAS(p + kAddressLane, kEmptyKey, na);
+    if (old == kEmptyKey) return na;
+    deallocate(T, na);
+    return old;
+}
+
 __device__ __forceinline__ unsigned long long pack_pair(uint32_t key, uint32_t value) {
     return ((unsigned long long)value << 32) | key;
 }

@@ -198,7 +198,10 @@ __global__ void bucket_kernel(TableView T, const uint32_t* keys, uint32_t* out, 
         out[i] = bucket_of(T, keys[i]);
 }
 
-// SlabAlloc microbenchmark: one request per lane, served one at a time per warp.
+// SlabAlloc microbenchmark: one request per lane. The paper's warp serves its
+// requests one at a time (warp_allocate, one atomic round trip each); `batched`
+// serves all 32 of a tile together (warp_allocate_many).
+template <bool kBatched>
 __global__ void alloc_kernel(TableView T, uint32_t* out, uint32_t n) {
     const uint32_t lane = lane_id();
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -207,14 +210,19 @@ __global__ void alloc_kernel(TableView T, uint32_t* out, uint32_t n) {
     bool failed = false;
     for (uint32_t tile = warp_gid; tile < (n + 31u) / 32u; tile += nwarps) {
         const uint32_t idx = tile * 32u + lane;
-        uint32_t queue = __ballot_sync(kFull, idx < n);
         uint32_t mine = kEmptyKey;
-        while (queue) {
-            const int s = __ffs(queue) - 1;
-            queue &= queue - 1u;
-            const uint32_t a = failed ? kAllocFailed : warp_allocate(T, ac, warp_gid);
-            if (a == kAllocFailed) failed = true;
-            if ((int)lane == s) mine = a;
+        if constexpr (kBatched) {
+            mine = failed ? kAllocFailed : warp_allocate_many(T, ac, warp_gid, idx < n);
+            failed = __any_sync(kFull, idx < n && mine == kAllocFailed);
+        } else {
+            uint32_t queue = __ballot_sync(kFull, idx < n);
+            while (queue) {
+                const int s = __ffs(queue) - 1;
+                queue &= queue - 1u;
+                const uint32_t a = failed ? kAllocFailed : warp_allocate(T, ac, warp_gid);
+                if (a == kAllocFailed) failed = true;
+                if ((int)lane == s) mine = a;
+            }
         }
         if (idx < n) out[idx] = mine;
     }
@@ -380,6 +388,30 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     return SLAB_OK;
 }
 
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): add the golden-ratio increment to the state, then
+// two xor-shift-multiply rounds and a final xor-shift.
+static uint64_t splitmix64(uint64_t& state) {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int slab_hash_params(uint64_t seed, uint32_t* hash_a, uint32_t* hash_b) {
+    if (!hash_a || !hash_b) return SLAB_ERR_INVALID_ARG;
+    uint64_t st = seed;
+    *hash_a = (uint32_t)(1 + splitmix64(st) % (kPrime - 1ull));
+    *hash_b = (uint32_t)(splitmix64(st) % kPrime);
+    return SLAB_OK;
+}
+
+int slab_create_seeded(uint32_t num_buckets, int mode, uint64_t seed, uint64_t pool_slabs, slab_table** out) {
+    uint32_t a = 0, b = 0;
+    slab_hash_params(seed, &a, &b);
+    return slab_create(num_buckets, mode, a, b, pool_slabs, out);
+}
+
 void slab_destroy(slab_table* t) {
     if (!t || !t->owns_memory) return;  // tables of a group are freed with the group
     cudaDeviceSynchronize();
@@ -540,13 +572,16 @@ int slab_alloc_batch(slab_table* t, uint32_t* d_addrs_out, uint32_t n, void* str
     if (n == 0) return SLAB_OK;
     const TableView T = view(t);
     const int tpb = t->cfg.threads_per_block;
+    const bool batched = t->cfg.variant == SLAB_VARIANT_STAGED;
+    const void* k = batched ? (const void*)alloc_kernel<true> : (const void*)alloc_kernel<false>;
     int bps = t->cfg.blocks_per_sm;
-    if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, alloc_kernel, tpb, 0) != cudaSuccess)
+    if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, tpb, 0) != cudaSuccess)
         return SLAB_ERR_CUDA;
     const uint64_t warps = (n + 31u) / 32u;
     const uint64_t want = (warps * 32 + tpb - 1) / tpb;
     const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
-    alloc_kernel<<<grid, tpb, 0, S(stream)>>>(T, d_addrs_out, n);
+    if (batched) alloc_kernel<true><<<grid, tpb, 0, S(stream)>>>(T, d_addrs_out, n);
+    else alloc_kernel<false><<<grid, tpb, 0, S(stream)>>>(T, d_addrs_out, n);
     return launch_rc();
 }
 

@@ -37,6 +37,7 @@ EXPORTED = [
     "slab_server_create", "slab_server_destroy", "slab_server_submit", "slab_server_collect",
     "slab_server_get_stats", "slab_server_run",
     "slab_set_multiset", "slab_search_all_batch", "slab_delete_all_batch", "slab_flush", "slab_grow_pool",
+    "slab_hash_params", "slab_create_seeded", "slab_probe_random_or",
 ]
 SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY = 64, 1 << 24, 1
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
@@ -128,6 +129,9 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_group_mixed": (i32, [vp, vp, vp, vp, vp, vp, vp, u32, vp]),
             "slab_group_status": (i32, [vp, vp, C.POINTER(u32)]),
             "slab_set_multiset": (i32, [vp, i32]),
+            "slab_hash_params": (i32, [u64, C.POINTER(u32), C.POINTER(u32)]),
+            "slab_create_seeded": (i32, [u32, i32, u64, u64, C.POINTER(vp)]),
+            "slab_probe_random_or": (i32, [vp, u64, u64, u32, i32, i32, vp]),
             "slab_search_all_batch": (i32, [vp, vp, u32, u32, vp, vp, vp]),
             "slab_delete_all_batch": (i32, [vp, vp, vp, u32, vp]),
             "slab_flush": (i32, [vp, C.POINTER(u64), vp]),
@@ -421,6 +425,26 @@ def slab_group_status(g: int, stream=None) -> tuple[int, int]:
     if rc == SLAB_ERR_CUDA or rc == SLAB_ERR_INVALID_ARG:
         raise SlabError(rc, "slab_group_status")
     return rc, flags.value
+
+
+def slab_hash_params(seed: int) -> tuple[int, int]:
+    a, b = C.c_uint32(0), C.c_uint32(0)
+    _check(load_library().slab_hash_params(int(seed), C.byref(a), C.byref(b)), "slab_hash_params")
+    return a.value, b.value
+
+
+def slab_create_seeded(num_buckets: int, mode: int, seed: int, pool_slabs: int) -> int:
+    h = C.c_void_p()
+    _check(load_library().slab_create_seeded(num_buckets, mode, int(seed), pool_slabs, C.byref(h)),
+           "slab_create_seeded")
+    return h.value
+
+
+def slab_probe_random_or(buf, footprint_words: int, n_ops: int, seed: int, ops_in_flight: int,
+                         threads_per_block: int, stream=None) -> None:
+    _check(load_library().slab_probe_random_or(_dptr(buf, 4, footprint_words, "buf"), footprint_words, n_ops, seed,
+                                               ops_in_flight, threads_per_block, _stream(stream)),
+           "slab_probe_random_or")
 
 
 # ------------------------------------------------------------------ paper variants

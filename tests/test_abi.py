@@ -83,3 +83,19 @@ def test_create_without_device_fails_cleanly(lib):
 def test_binding_rejects_host_tensors(lib):
     with pytest.raises(ValueError):
         sh.slab_search_batch(1, torch.zeros(4, dtype=torch.int32), torch.zeros(4, dtype=torch.int32))
+
+
+def test_seeded_hash_parameters(lib):
+    """slab_hash_params draws a = 1 + x1 mod (p - 1), b = x2 mod p from the first two
+    SplitMix64 outputs; for seed 0 those are the generator's published reference
+    values 0xE220A8397B1DCDAF and 0x6E789E6AA1B965F4."""
+    P = sh.SLAB_HASH_PRIME
+    a, b = sh.slab_hash_params(0)
+    assert a == 1 + 0xE220A8397B1DCDAF % (P - 1) and b == 0x6E789E6AA1B965F4 % P
+    seen = set()
+    for seed in range(200):
+        a, b = sh.slab_hash_params(seed)
+        assert 1 <= a < P and 0 <= b < P and (a, b) == sh.slab_hash_params(seed)
+        seen.add((a, b))
+    assert len(seen) == 200
+    assert lib.slab_hash_params(1, None, None) == sh.SLAB_ERR_INVALID_ARG

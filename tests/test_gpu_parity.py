@@ -3,10 +3,10 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import hash_of
+from oracle import OracleTable, hash_of
 from paper_1710_11246_gb300 import slabhash as sh
 from paper_1710_11246_gb300 import workload as W
-from tests.gpu_helpers import VARIANTS, Pair, dev, host
+from tests.gpu_helpers import VARIANTS, Pair, dev, host, u8
 
 pytestmark = pytest.mark.gpu
 
@@ -301,15 +301,18 @@ def test_side_stream():
         p.close()
 
 
-def test_slab_alloc_microbench_state():
-    """Sec. 5 SlabAlloc: n single-slab allocations give n distinct valid addresses,
-    the bitmaps mark exactly those units, and freeing them all clears every bit."""
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_slab_alloc_microbench_state(variant):
+    """Sec. 5 SlabAlloc, one request per lane served one at a time (direct) or all
+    32 of a warp together (staged): n single-slab allocations give n distinct valid
+    addresses, the bitmaps mark exactly those units, and freeing them all clears
+    every bit."""
     from oracle import check_alloc
     t = sh.SlabHash(8, 3, 4, pool_slabs=1 << 17)
     try:
         n = 100000
         addrs = torch.empty(n, dtype=torch.int32, device="cuda")
-        t.configure(random_probes=64)
+        t.configure(random_probes=64, variant=VARIANTS[variant])
         sh.slab_alloc_batch(t.handle, addrs)
         rc, flags = t.status()
         assert rc == sh.SLAB_OK, flags
@@ -330,3 +333,25 @@ def test_slab_alloc_microbench_state():
         assert check_alloc(a[good], host(t.bitmaps()), t.info.num_memory_blocks) == (0, 0)
     finally:
         t.close()
+
+
+def test_create_seeded_uses_the_seeded_parameters():
+    """slab_create_seeded draws (a, b) with slab_hash_params and reports them; a table
+    built that way agrees with the oracle on those parameters."""
+    w = W.config1(seed=0)
+    h = sh.slab_create_seeded(w.num_buckets, sh.SLAB_MODE_KEY_VALUE, 1234, 4096)
+    try:
+        info = sh.slab_get_info(h)
+        assert (info.hash_a, info.hash_b) == sh.slab_hash_params(1234)
+        o = OracleTable(w.num_buckets, info.hash_a, info.hash_b)
+        fd = torch.empty(len(w.keys), dtype=torch.uint8, device="cuda")
+        sh.slab_insert_batch(h, dev(w.keys), dev(w.values), fd)
+        o.insert(w.keys, w.values)
+        vals = torch.empty(len(w.search.keys), dtype=torch.int32, device="cuda")
+        found = torch.empty(len(w.search.keys), dtype=torch.uint8, device="cuda")
+        sh.slab_search_batch(h, dev(w.search.keys), vals, found)
+        vo, fo = o.search(w.search.keys)
+        assert (host(vals) == vo).all() and (u8(found) == fo).all()
+        o.close()
+    finally:
+        sh.slab_destroy(h)
