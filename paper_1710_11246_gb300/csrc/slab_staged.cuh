@@ -231,25 +231,37 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                 }
             }
         }
-        // full lists grow by one slab each: lanes whose lists end in the same slab
-        // elect one leader, the leaders get their slabs in one batched SlabAlloc
-        // round (Sec. 5) and link them with their own CAS, and the other lanes
-        // follow their leader (so a warp holds at most one unlinked slab per list)
-        if (__any_sync(kFull, need_slab)) {
-            const uint32_t peers = __match_any_sync(kFull, need_slab ? (unsigned long long)gslab : 0ull);
-            const int leader = __ffs(peers) - 1;
-            const uint32_t lead_nx = grow_lists(T, ac, warp_gid, gslab, need_slab && (int)lane == leader);
-            const uint32_t nx = __shfl_sync(kFull, lead_nx, leader);
-            if (need_slab) {
-                if (nx == kAllocFailed) {
-                    set_flag(T, kFlagOutOfSlabs);
-                    pending = false;
-                } else if (valid_next(T, nx)) {
-                    cur = nx;
-                } else {
-                    set_flag(T, kFlagBadPointer);
-                    pending = false;
-                }
+        // full lists grow by one slab each (SlabAlloc, Sec. 5)
+        auto settle = [&](uint32_t nx) {
+            if (nx == kAllocFailed) {
+                set_flag(T, kFlagOutOfSlabs);
+                pending = false;
+            } else if (valid_next(T, nx)) {
+                cur = nx;
+            } else {
+                set_flag(T, kFlagBadPointer);
+                pending = false;
+            }
+        };
+        if constexpr (kKind == kKindInsert) {
+            // bulk builds grow many lists at once: lanes whose lists end in the same
+            // slab elect one leader, the leaders get their slabs in one batched
+            // SlabAlloc round and link them with their own CAS, and the other lanes
+            // follow their leader (a warp holds at most one unlinked slab per list)
+            if (__any_sync(kFull, need_slab)) {
+                const uint32_t peers = __match_any_sync(kFull, need_slab ? (unsigned long long)gslab : 0ull);
+                const int leader = __ffs(peers) - 1;
+                const uint32_t lead_nx = grow_lists(T, ac, warp_gid, gslab, need_slab && (int)lane == leader);
+                const uint32_t nx = __shfl_sync(kFull, lead_nx, leader);
+                if (need_slab) settle(nx);
+            }
+        } else if constexpr (kKind == kKindMixed) {
+            // mixed batches grow a list now and then: one lane at a time
+            for (uint32_t q = __ballot_sync(kFull, need_slab); q; q &= q - 1u) {
+                const int s = __ffs(q) - 1;
+                uint32_t* ps = reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)gslab, s));
+                const uint32_t nx = grow_list(T, ac, warp_gid, ps, s);
+                if ((int)lane == s) settle(nx);
             }
         }
         if (pending && ++rounds >= T.iter_limit) {
