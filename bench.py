@@ -190,6 +190,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- GPU arm
+def slowest_rank_ms(local_ms: float, world: int) -> float:
+    """The job's time: the largest of the ranks' timed totals (replicas run the same
+    workload each, so the slowest one decides when all of them are done)."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    x = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def job_value(ms_per_step: float, world: int) -> float:
+    """Whole-job Mops/s: every rank runs OPS_PER_STEP per step (weak scaling)."""
+    return OPS_PER_STEP * world / (ms_per_step * 1e3)
+
+
 def gpu_arm(args, rank, world, device):
     import torch
 
@@ -304,11 +322,7 @@ def gpu_arm(args, rank, world, device):
         raise RuntimeError(f"device status after timed steps: rc={rc} flags={flags}")
     step_ms = [evs[0].elapsed_time(evs[3]) for evs in timed]
     dom_ms = [evs[1].elapsed_time(evs[2]) for evs in timed]
-    total_ms = sum(step_ms)
-    if world > 1:
-        x = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(x, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(x.item())
+    total_ms = slowest_rank_ms(sum(step_ms), world)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -913,7 +927,7 @@ def main():
         return
 
     ms_step = r["total_ms"] / args.steps
-    value = OPS_PER_STEP * world / (ms_step * 1e3)  # Mops/s over all ranks
+    value = job_value(ms_step, world)  # Mops/s over all ranks
     mean = {p: statistics.fmean(v) for p, v in r["per_phase"].items()}
     ops = {"build": N_KEYS, "search": N_SEARCH, "delete": N_DELETE, "mixed": N_MIXED}
     per_op = {p: round(ops[p] / (mean[p] * 1e3), 1) for p in ops}
