@@ -433,6 +433,7 @@ typedef struct slab_server_stats {
                                  found every slot busy */
     uint64_t deferred_memory; /* head-of-queue requests held back by the pool bound while others ran */
     uint64_t rejected_memory; /* requests refused: the pool bound failed with nothing in flight */
+    uint64_t pool_grown;      /* pool growths (SLAB_SERVER_GROW_POOL) */
     uint64_t pool_slabs;      /* the table's pool size */
     uint64_t pool_measured;   /* latest allocated-slab count */
     uint64_t pool_reserved;   /* inserts of requests whose count is outstanding */
@@ -442,12 +443,15 @@ typedef struct slab_server_stats {
 /* t: a table on the current device (it may already hold keys); 1 <= slots <=
  * SLAB_SERVER_MAX_SLOTS; 1 <= max_request_ops <= SLAB_SERVER_MAX_REQUEST_OPS
  * (a slot's capacity: the largest request, and the largest batch
- * slab_server_run packs); 0 < pool_high_water <= 1; flags: 0 or
- * SLAB_SERVER_ZERO_COPY. Allocates the slots and measures the pool in use.
+ * slab_server_run packs); 0 < pool_high_water <= 1; flags: any of
+ * SLAB_SERVER_ZERO_COPY, SLAB_SERVER_GROW_POOL. Allocates the slots and measures the pool in use.
  * Errors: SLAB_ERR_INVALID_ARG for bad arguments or a table of another device;
  * SLAB_ERR_CUDA when an allocation fails (nothing is kept). */
 #define SLAB_SERVER_ZERO_COPY 0x1u /* slab_server_run: kernels read and write page-locked, device-mapped
                                       caller arrays in place instead of copying them */
+#define SLAB_SERVER_GROW_POOL 0x2u /* a request the pool bound refuses while nothing is in flight grows
+                                      the pool (slab_grow_pool, by at least half) instead of failing;
+                                      the table must own its memory (not a group's) */
 int slab_server_create(slab_table *t, uint32_t slots, uint32_t max_request_ops, double pool_high_water,
                        uint32_t flags, slab_server **out);
 /* Waits for every slot's stream, then frees the server (not the table). */

@@ -33,7 +33,9 @@
 // starts after its own batch ends, on its stream, and reads the bitmaps through
 // L2, so the count that started last sees every allocation of every batch
 // folded in before it; allocation never shrinks on this path (deletes leave
-// tombstones). The bound therefore always covers the pool in use.
+// tombstones). The bound therefore always covers the pool in use. With
+// SLAB_SERVER_GROW_POOL a request that does not fit while nothing is in flight
+// grows the pool (slab_grow_pool) instead of being refused.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -331,6 +333,18 @@ HostMem host_mem(const void* p) {
     return {true, a.devicePointer};
 }
 
+// Grow the table's pool (Sec. 5, more super blocks) so that `inserts` more fit
+// under the bound: by at least half of the current pool, to keep growth rare.
+// Only called with nothing in flight on the server's slots.
+int grow_for(slab_server* sv, uint64_t inserts) {
+    slab_table* t = sv->table;
+    const double need = (double)(sv->measured + sv->reserved + inserts) / sv->high_water - (double)t->pool_slabs;
+    const uint64_t extra = std::max<uint64_t>((uint64_t)need + 1, t->pool_slabs / 2);
+    const int rc = slab_grow_pool(t, extra);
+    if (rc == SLAB_OK) sv->stats.pool_grown++;
+    return fits(sv, inserts) ? rc : SLAB_ERR_OUT_OF_SLABS;
+}
+
 using Clock = std::chrono::steady_clock;
 inline uint64_t ns_since(Clock::time_point t0) {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
@@ -346,7 +360,7 @@ int slab_server_create(slab_table* t, uint32_t slots, uint32_t max_request_ops, 
     *out = nullptr;
     if (!t || slots == 0 || slots > SLAB_SERVER_MAX_SLOTS || max_request_ops == 0 ||
         max_request_ops > SLAB_SERVER_MAX_REQUEST_OPS || !(pool_high_water > 0.0) || pool_high_water > 1.0 ||
-        (flags & ~SLAB_SERVER_ZERO_COPY))
+        (flags & ~(SLAB_SERVER_ZERO_COPY | SLAB_SERVER_GROW_POOL)))
         return SLAB_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return SLAB_ERR_CUDA;
@@ -401,8 +415,12 @@ int slab_server_submit(slab_server* sv, const uint8_t* h_ops, const uint32_t* h_
     }
     const uint64_t k = count_inserts(h_ops, n);
     if (!fits(sv, k)) {
-        sv->stats.deferred_memory++;
-        return SLAB_ERR_OUT_OF_SLABS;
+        bool any_busy = false;
+        for (const Slot& o : sv->slots) any_busy |= o.busy;
+        if (any_busy || !(sv->flags & SLAB_SERVER_GROW_POOL) || grow_for(sv, k) != SLAB_OK) {
+            sv->stats.deferred_memory++;
+            return SLAB_ERR_OUT_OF_SLABS;
+        }
     }
     // the caller may reuse its arrays as soon as this returns: always staged
     const Io io{kStaged, kStaged, h_ops, h_keys, h_values, nullptr, nullptr};
@@ -529,7 +547,9 @@ int slab_server_run(slab_server* sv, uint64_t n_requests, const uint64_t* h_arri
                     if (held_memory != next) sv->stats.deferred_memory++, held_memory = next;
                     break;
                 }
-                // nothing in flight: the pool cannot take this request now or later
+                // nothing in flight: grow the pool if allowed, else the pool cannot
+                // take this request now or later
+                if ((sv->flags & SLAB_SERVER_GROW_POOL) && grow_for(sv, inserts[next]) == SLAB_OK) continue;
                 if (h_wait_ns) h_wait_ns[next] = now - h_arrival_ns[next];
                 sv->stats.rejected_memory++;
                 complete(next++, now, SLAB_ERR_OUT_OF_SLABS);

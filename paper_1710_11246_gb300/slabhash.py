@@ -39,7 +39,7 @@ EXPORTED = [
     "slab_set_multiset", "slab_search_all_batch", "slab_delete_all_batch", "slab_flush", "slab_grow_pool",
     "slab_hash_params", "slab_create_seeded", "slab_probe_random_or",
 ]
-SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY = 64, 1 << 24, 1
+SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY, SLAB_SERVER_GROW_POOL = 64, 1 << 24, 1, 2
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
 MODEL_FLOATS = 2 + 2 * 1024
 
@@ -66,7 +66,8 @@ class SlabLearnReport(C.Structure):
 class SlabServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("batches", C.c_uint64),
                 ("deferred_slot", C.c_uint64),
-                ("deferred_memory", C.c_uint64), ("rejected_memory", C.c_uint64), ("pool_slabs", C.c_uint64),
+                ("deferred_memory", C.c_uint64), ("rejected_memory", C.c_uint64), ("pool_grown", C.c_uint64),
+                ("pool_slabs", C.c_uint64),
                 ("pool_measured", C.c_uint64), ("pool_reserved", C.c_uint64), ("inflight", C.c_uint32),
                 ("pad", C.c_uint32)]
 

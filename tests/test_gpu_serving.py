@@ -136,6 +136,31 @@ def test_admission_by_free_pool_memory():
         p.close()
 
 
+def test_pool_grows_instead_of_refusing():
+    """With SLAB_SERVER_GROW_POOL the same trace that overflowed the pool is served
+    in full: the pool grows between batches, nothing is refused, and every request
+    agrees with the oracle."""
+    tr = W.serving_trace(1 << 16, 200, None, ratios=(0.6, 0.1, 0.3), max_size=1 << 12, seed=5)
+    p = _loaded_pair(tr, pool_slabs=2048)
+    sv = sh.slab_server_create(p.g.handle, 8, 1 << 12, pool_high_water=0.95, flags=sh.SLAB_SERVER_GROW_POOL)
+    try:
+        out = sh.slab_server_run(sv, tr.arrival_ns, tr.op_start, tr.ops, tr.keys, tr.values)
+        st = sh.slab_server_get_stats(sv)
+        assert (out["status"] == sh.SLAB_OK).all() and st["rejected_memory"] == 0
+        assert st["pool_grown"] >= 1 and sh.slab_get_info(p.g.handle).pool_slabs > 2048
+        _check_against_oracle(p, tr, out, np.ones(200, bool))
+        # submit grows too, with nothing in flight
+        big = np.arange(1, 40001, dtype=np.uint32) | np.uint32(1 << 30)
+        before = sh.slab_get_info(p.g.handle).pool_slabs
+        rc, ticket = sh.slab_server_submit(sv, np.zeros(4000, np.uint8), big[:4000], big[:4000])
+        assert rc == sh.SLAB_OK
+        sh.slab_server_collect(sv, ticket, 4000)
+        assert sh.slab_get_info(p.g.handle).pool_slabs >= before
+    finally:
+        sh.slab_server_destroy(sv)
+        p.close()
+
+
 def test_submit_collect_slots_and_errors():
     tr = W.serving_trace(1 << 12, 4, None, max_size=300, seed=9)
     p = _loaded_pair(tr)
