@@ -198,8 +198,9 @@ int slab_status(slab_table *t, void *stream, uint32_t *h_flags);
  * slots of each list (live plus tombstones). d_slabs (nullable): B uint32,
  * slabs of each list (base slab included). h_totals (nullable): 6 uint64 =
  * {live elements, used slots, slabs, pool slabs marked allocated in the
- * bitmaps, lists whose used slots are not a prefix in (slab, lane) order,
- * slabs linked from a list}. Memory utilization (Sec. 3.3) is
+ * bitmaps, lists whose used slots are not a prefix in (slab, lane) order
+ * (always 0 for a set table; a multiset table's deletes leave holes), slabs
+ * linked from a list}. Memory utilization (Sec. 3.3) is
  * (x / 128) * live / slabs with x = 8 (pairs) or 4 (keys). Synchronizes
  * `stream` when h_totals is given.
  */
