@@ -355,3 +355,62 @@ def test_create_seeded_uses_the_seeded_parameters():
         o.close()
     finally:
         sh.slab_destroy(h)
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("key_only", [False, True])
+def test_repeated_keys_in_one_batch_follow_a_serial_order(variant, key_only):
+    """Ops of one batch are concurrent; with a key repeated, every outcome must be one
+    that some serial order of the ops produces: keys stay unique, exactly one of a
+    new key's inserts reports it new, the stored value is one the batch wrote, and
+    searches see the key's value before or after the batch's writes."""
+    ks = W.KeyStream(41)
+    pre = ks.take(6000)
+    new = ks.take(3000)
+    B = W.buckets_for(9000, 0.6)
+    p = Pair(B, 17, 23, variant=variant, key_only=key_only, n_hint=12000)
+    try:
+        p.insert(pre, None if key_only else W.values_for(pre))
+        rng = np.random.default_rng(42)
+        gone = pre[:2000]
+        ops = np.concatenate([np.full(3000, 0, np.uint8), np.full(3000, 0, np.uint8), np.full(3000, 2, np.uint8),
+                              np.full(2000, 1, np.uint8), np.full(2000, 2, np.uint8)])
+        keys = np.concatenate([new, new, new, gone, gone]).astype(np.uint32)
+        v1, v2 = (new * np.uint32(3)).astype(np.uint32), (new * np.uint32(5)).astype(np.uint32)
+        vals = np.concatenate([v1, v2, np.zeros(7000, np.uint32)]).astype(np.uint32)
+        perm = rng.permutation(len(keys))
+        fd = torch.empty(len(keys), dtype=torch.uint8, device="cuda")
+        res = host(p.g.mixed(torch.from_numpy(ops[perm]).cuda(), dev(keys[perm]),
+                             None if key_only else dev(vals[perm]), found=fd))
+        fnd = u8(fd)
+        r, f = np.empty_like(res), np.empty_like(fnd)
+        r[perm], f[perm] = res, fnd
+        rc, flags = p.g.status()
+        assert flags == 0
+        # the two inserts of each new key: exactly one found it absent
+        f_ins = f[:3000] + f[3000:6000]
+        assert (f_ins == 1).all() and ((r[:3000] + r[3000:6000]) == 1).all()
+        # deletes of preloaded keys all hit
+        assert (f[9000:11000] == 1).all() and (r[9000:11000] == 1).all()
+        # searches: before or after the batch's writes
+        s_new, sf_new = r[6000:9000], f[6000:9000]
+        if key_only:
+            assert ((s_new == 0) | (s_new == sh.SLAB_NOT_FOUND)).all()
+        else:
+            assert ((sf_new == 0) & (s_new == sh.SLAB_NOT_FOUND) | (sf_new == 1) & ((s_new == v1) | (s_new == v2))).all()
+        s_gone, sf_gone = r[11000:], f[11000:]
+        want = 0 if key_only else W.values_for(gone)
+        assert ((sf_gone == 0) & (s_gone == sh.SLAB_NOT_FOUND) | (sf_gone == 1) & (s_gone == want)).all()
+        # afterwards: new keys once each with a value the batch wrote, deleted keys gone
+        fd2 = torch.empty(3000, dtype=torch.uint8, device="cuda")
+        vals_now = host(p.g.search(dev(new), found=fd2))
+        assert (u8(fd2) == 1).all()
+        if not key_only:
+            assert ((vals_now == v1) | (vals_now == v2)).all()
+        fd3 = torch.empty(2000, dtype=torch.uint8, device="cuda")
+        p.g.search(dev(gone), found=fd3)
+        assert (u8(fd3) == 0).all()
+        tot = p.g.stats()
+        assert tot["live"] == 6000 - 2000 + 3000 and tot["prefix_violations"] == 0
+    finally:
+        p.close()
