@@ -77,6 +77,27 @@ def test_trace_matches_oracle(slots, rate, capacity, pinned, zero_copy):
         p.close()
 
 
+@pytest.mark.parametrize("zero_copy", [False, True])
+def test_key_only_table_serving(zero_copy):
+    """A key-only table behind the server: values are ignored, results are the
+    key-only ones (search 0 / NOT_FOUND, insert and delete 1 / 0), all equal to the
+    oracle's."""
+    tr = W.serving_trace(1 << 15, 150, None, max_size=1 << 11, seed=33)
+    p = Pair(tr.num_buckets, tr.hash_a, tr.hash_b, key_only=True, n_hint=1 << 16)
+    p.insert(tr.preload)
+    arrays = [sh.pinned_copy(tr.ops), sh.pinned_copy(tr.keys), None]
+    sv = sh.slab_server_create(p.g.handle, 4, 1 << 13, flags=sh.SLAB_SERVER_ZERO_COPY if zero_copy else 0)
+    try:
+        out = sh.slab_server_run(sv, tr.arrival_ns, tr.op_start, *arrays, pinned_outputs=zero_copy)
+        assert (out["status"] == sh.SLAB_OK).all()
+        ro, fo = p.o.mixed(tr.ops, tr.keys, None)
+        assert (out["results"] == ro).all() and (out["found"] == fo).all()
+        p.check_structure()
+    finally:
+        sh.slab_server_destroy(sv)
+        p.close()
+
+
 def test_each_request_same_alone_and_in_the_mix():
     """Results of requests served eight at a time equal, bit for bit, the results
     of the same requests each run alone on a freshly loaded table."""
