@@ -569,6 +569,10 @@ def sweep(args, device):
         serving_sweep(args, device, stream, flush)
     if want("flush"):
         flush_sweep(args, device, stream, flush)
+    if want("sizes"):
+        sizes_sweep(args, device, stream, flush)
+    if want("incremental"):
+        incremental_sweep(args, device, stream, flush)
     if not want("mixed"):
         return
     # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
@@ -888,6 +892,92 @@ def flush_sweep(args, device, stream, flush):
     t.close()
 
 
+def sizes_sweep(args, device, stream, flush):
+    """Rates against table size at a fixed mean of 0.6 slabs per bucket (about 55 %
+    memory utilization, the paper's bulk benchmark over table sizes, Sec. 6.1):
+    build, search at 0 % and 100 % hit, n = 2^16 .. 2^24."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
+    rows = []
+    for lg in (16, 18, 20, 22, 24):
+        n = 1 << lg
+        ks = W.KeyStream(args.seed + lg)
+        keys = ks.take(n)
+        absent = ks.take(n)
+        rng = np.random.default_rng([args.seed, lg])
+        B = W.buckets_for(n, BETA)
+        a, b = W.hash_params(args.seed + lg)
+        t = sh.SlabHash(B, a, b, max(1024, n // 8))
+        h = t.handle
+        kb, vb, kq, ka = dev(keys), dev(W.values_for(keys)), dev(keys[rng.permutation(n)]), dev(absent)
+        out = torch.empty(n, dtype=torch.int32, device=device)
+
+        def build():
+            sh.slab_reset(h, stream)
+            sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+        ms_b = min(_time_ms(build, stream, flush) for _ in range(3))
+        with torch.cuda.stream(stream):
+            build()
+        ms_hit = min(_time_ms(lambda: sh.slab_search_batch(h, kq, out, None, stream=stream), stream, flush)
+                     for _ in range(3))
+        ms_miss = min(_time_ms(lambda: sh.slab_search_batch(h, ka, out, None, stream=stream), stream, flush)
+                      for _ in range(3))
+        rc, _ = t.status(stream)
+        tot = t.stats()
+        rows.append({"n": n, "num_buckets": B, "build_incl_reset": round(n / (ms_b * 1e3), 1),
+                     "search_100": round(n / (ms_hit * 1e3), 1), "search_0": round(n / (ms_miss * 1e3), 1),
+                     "utilization": round(8.0 * tot["live"] / (128.0 * tot["slabs"]), 4), "status": rc})
+        t.close()
+    print(json.dumps({"sweep": "sizes", "beta": BETA, "unit": "Mops/s", "rows": rows}), flush=True)
+
+
+def incremental_sweep(args, device, stream, flush):
+    """Incremental insertion (the slab hash's half of the paper's Sec. 6.2
+    experiment): 2^21 elements inserted in batches of 2^15, 2^16 or 2^17 into a table
+    sized for the final count (beta 0.6); mean insert rate over the batches."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
+    total = 1 << 21
+    keys = W.KeyStream(args.seed + 99).take(total)
+    B = W.buckets_for(total, BETA)
+    a, b = W.hash_params(args.seed + 99)
+    kb, vb = dev(keys), dev(W.values_for(keys))
+    t = sh.SlabHash(B, a, b, 1 << 18)
+    h = t.handle
+    line = {"sweep": "incremental", "elements": total, "num_buckets": B, "unit": "Mops/s",
+            "launch": "the batches replayed from one CUDA graph (host launch cost excluded)"}
+    with torch.cuda.stream(stream):  # warm-up: the launch path caches its occupancy query
+        sh.slab_insert_batch(h, kb[:32], vb[:32], None, n=32, stream=stream)
+    torch.cuda.synchronize()
+    for lg in (15, 16, 17):
+        bs = 1 << lg
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for i in range(0, total, bs):
+                sh.slab_insert_batch(h, kb[i:i + bs], vb[i:i + bs], None, n=bs, stream=stream)
+        with torch.cuda.stream(stream):
+            sh.slab_reset(h, stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rc, _ = t.status(stream)
+        line[f"batch_{bs}"] = {"batches": total // bs, "mops": round(total / (ms * 1e3), 1), "status": rc}
+    tot = t.stats()
+    line["live"] = tot["live"]
+    print(json.dumps(line), flush=True)
+    t.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -901,7 +991,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--sweep", nargs="?", const="all", default=None,
-                    choices=["all", "bulk", "slaballoc", "learned", "group", "serving", "flush", "mixed"],
+                    choices=["all", "bulk", "slaballoc", "learned", "group", "serving", "flush", "sizes", "incremental",
+                             "mixed"],
                     help="print the sweep lines (all, or one section) instead of the step line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
