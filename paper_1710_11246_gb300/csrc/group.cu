@@ -44,7 +44,7 @@ struct slab_group {
 
 namespace {
 
-constexpr uint32_t kGroupWordsPerWarp = kStagedWordsPerWarp;  // the staged kernels' per-warp layout
+constexpr uint32_t kGroupWordsPerWarp = kServeWordsPerWarp;  // stage, ballots, keys, alternate keys
 
 // Tiles of table i: ceil(ops / 32); a decreasing pair of starts counts as no ops.
 __device__ __forceinline__ uint32_t tiles_of(const uint32_t* op_start, uint32_t i) {

@@ -23,6 +23,13 @@
 // Staging just before serving (rather than a tile ahead into a second buffer)
 // keeps one 4 KB stage per warp, which leaves room for more resident warps, and
 // gives claims a fresh snapshot (an older one makes them lose more races).
+//
+// Search and delete batches do not restage inside a tile: an op that must go on
+// to its list's next slab waits in a per-warp ring and is served later in a
+// tile of such ops, 32 at a time, so one long list does not hold the whole warp
+// for another stage-and-match round. Insert and mixed batches serve each tile
+// to the end: their rounds also claim pairs and grow lists, and measured slower
+// when deferred.
 #pragma once
 #include "slab_device.cuh"
 #include "slab_wcws.cuh"
@@ -33,7 +40,12 @@ constexpr uint32_t kTileWords = 32u * kWordsPerSlab;  // one slab per lane: 4 KB
 constexpr uint32_t kNoOpCode = 0xFFu;
 // per warp: the stage, then 32 ballot words, the tile's 32 keys and, for mixed
 // batches, 32 alternate keys (below)
-constexpr uint32_t kStagedWordsPerWarp = kTileWords + 32u + 32u + 32u;
+constexpr uint32_t kServeWordsPerWarp = kTileWords + 32u + 32u + 32u;
+// Search and delete kernels add the ring of deferred ops behind that: op index,
+// slab to stage next, key and rounds so far, kDeferSlots of each. The largest
+// per-warp layout of the staged kernels is kStagedWordsPerWarp.
+constexpr uint32_t kDeferSlots = 64u;
+constexpr uint32_t kStagedWordsPerWarp = kServeWordsPerWarp + 4u * kDeferSlots;
 
 // The second value a mixed op's WCWS step matches besides its key: an empty
 // slot for an insert (it may claim one), its key again for a search or delete.
@@ -79,6 +91,75 @@ __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, 
         const uint32_t us = __shfl_sync(kFull, u, 4u * j + g);
         if ((mg >> (4u * j)) & 1u)
             cp_async_16(((j & 1u) ? dst_odd : dst_even) + j * 512u, src + (uint64_t)us * kWordsPerSlab);
+    }
+}
+
+// One WCWS round (Fig. "alg:search") of a search or delete batch for the ops of
+// the lanes in `pend`, each of whose current slab (unified index u) is staged in
+// slot `lane` of `buf`, with keys in `skeys`: the warp takes the queued ops in
+// lane order and finds each one's matching lanes by ballot, then every source
+// lane acts on its ballot (reads the value, or writes the tombstone). On return
+// an op that is done has its result in res / fnd and pending cleared; one that
+// goes on has u set to its list's next slab.
+template <int kKind, bool kKeyOnly>
+__device__ __forceinline__ void read_round(const TableView& T, const uint32_t* buf, uint32_t* ballots,
+                                           const uint32_t* skeys, const uint32_t (&off)[8], uint32_t pend,
+                                           bool& pending, uint32_t& u, uint32_t& res, uint32_t& fnd) {
+    static_assert(kKind == kKindSearch || kKind == kKindDelete, "claims serve whole tiles (serve_tile)");
+    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    const uint32_t lane = lane_id();
+    auto step = [&](uint32_t s, uint32_t data) {
+        const uint32_t mm = __ballot_sync(kFull, data == skeys[s]);
+        if (lane == 0) ballots[s] = mm;
+    };
+    if (pend == kFull) {
+        // four ops per key load and per ballot store, no branches
+#pragma unroll
+        for (uint32_t g = 0; g < 8; ++g) {
+            const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
+            const uint32_t s0 = 4u * g;
+            uint4 b4;
+            b4.x = __ballot_sync(kFull, buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]] == k4.x);
+            b4.y = __ballot_sync(kFull, buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]] == k4.y);
+            b4.z = __ballot_sync(kFull, buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]] == k4.z);
+            b4.w = __ballot_sync(kFull, buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]] == k4.w);
+            if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
+        }
+    } else if (__popc(pend) > 8) {
+#pragma unroll
+        for (uint32_t s = 0; s < 32; ++s)
+            if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
+    } else {
+        for (uint32_t q = pend; q; q &= q - 1u) {
+            const uint32_t s = (uint32_t)(__ffs(q) - 1);
+            step(s, buf[swz(s, lane)]);
+        }
+    }
+    __syncwarp();
+    // the source lanes act on their ballots (Sec. 4.3)
+    const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
+    if (pending) {
+        if (m) {
+            const uint32_t d = (uint32_t)(__ffs(m) - 1);
+            if constexpr (kKind == kKindSearch) {
+                res = kKeyOnly ? 0u : buf[swz(lane, d + 1u)];
+            } else {
+                remove_at<kKeyOnly>(T, T.slabs + (uint64_t)u * kWordsPerSlab, d);
+                res = 1u;
+            }
+            fnd = 1u;
+            pending = false;
+        } else {
+            const uint32_t nx = buf[swz(lane, kAddressLane)];
+            if (nx == kEmptyKey) {
+                pending = false;  // end of the list: not found
+            } else if (valid_next(T, nx)) {
+                u = T.num_buckets + nx;
+            } else {
+                set_flag(T, kFlagBadPointer);
+                pending = false;
+            }
+        }
     }
 }
 
@@ -289,6 +370,9 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
 
 template <int kKind>
 constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
+// shared memory words per warp of a kind's kernel (the ring only where ops wait in one)
+template <int kKind>
+constexpr uint32_t kWordsPerWarp = kClaims<kKind> ? kServeWordsPerWarp : kStagedWordsPerWarp;
 
 template <int kKind, bool kKeyOnly>
 __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXNREG)
@@ -296,10 +380,14 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
     const uint32_t lane = lane_id();
-    uint32_t* buf = smem + (threadIdx.x >> 5) * kStagedWordsPerWarp;
+    uint32_t* buf = smem + (threadIdx.x >> 5) * kWordsPerWarp<kKind>;
     uint32_t* ballots = buf + kTileWords;
     uint32_t* skeys = ballots + 32;
     uint32_t* salts = skeys + 32;
+    uint32_t* q_idx = salts + 32;  // the ring (search and delete kernels)
+    uint32_t* q_u = q_idx + kDeferSlots;
+    uint32_t* q_key = q_u + kDeferSlots;
+    uint32_t* q_rounds = q_key + kDeferSlots;
     const uint32_t buf_s = (uint32_t)__cvta_generic_to_shared(buf);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -333,6 +421,28 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
     };
     auto walks = [](uint32_t k, uint32_t o) { return o <= kOpSearch && k < kTombstone; };
 
+    // Search / delete ops that must go on to another slab wait in a ring of
+    // kDeferSlots entries; qh / qn: its head and count (warp-uniform).
+    uint32_t qh = 0u, qn = 0u;
+    auto push = [&](bool keep, uint32_t i, uint32_t uu, uint32_t k, uint32_t r) {
+        const uint32_t b = __ballot_sync(kFull, keep);
+        if (keep) {
+            const uint32_t pos = (qh + qn + __popc(b & ((1u << lane) - 1u))) & (kDeferSlots - 1u);
+            q_idx[pos] = i;
+            q_u[pos] = uu;
+            q_key[pos] = k;
+            q_rounds[pos] = r;
+        }
+        qn += __popc(b);
+        __syncwarp();
+    };
+    auto round_done = [&](bool& pending, uint32_t& r) {
+        if (pending && ++r >= T.iter_limit) {
+            set_flag(T, kFlagIterLimit);
+            pending = false;
+        }
+    };
+
     // prologue: this tile hashed (its base slabs pulled into L2 for big tables),
     // the next tile loading
     uint32_t ck, cv, co;
@@ -359,8 +469,59 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
         cp_async_wait<0>();
         __syncwarp();
         const uint32_t idx = t * 32u + lane;
-        serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb, idx,
-                                    idx < A.n);
+        if constexpr (kClaims<kKind>) {
+            serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb,
+                                        idx, idx < A.n);
+        } else {
+            // the tile's first round; the ops that go on join the ring
+            if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
+            bool pending = walks(ck, co);
+            const uint32_t pend = __ballot_sync(kFull, pending);
+            uint32_t res = default_result(co), fnd = 0u, u = cb, r = 0u;
+            if (pend) {
+                read_round<kKind, kKeyOnly>(T, buf, ballots, skeys, off, pend, pending, u, res, fnd);
+                round_done(pending, r);
+            }
+            if (idx < A.n && !pending) {
+                if (A.results) A.results[idx] = res;
+                if (A.found) A.found[idx] = (uint8_t)fnd;
+            }
+            __syncwarp();
+            push(pending, idx, u, ck, r);
+            // tiles of waiting ops: whenever 32 wait, and after the warp's last
+            // tile until the ring is empty
+            const bool last = t + nwarps >= ntiles;
+            while (qn >= 32u || (last && qn)) {
+                const uint32_t take = qn < 32u ? qn : 32u;
+                const bool mine = lane < take;
+                const uint32_t pos = (qh + lane) & (kDeferSlots - 1u);
+                uint32_t i = 0u, uu = 0u, k = 0u, rr = 0u;
+                if (mine) {
+                    i = q_idx[pos];
+                    uu = q_u[pos];
+                    k = q_key[pos];
+                    rr = q_rounds[pos];
+                }
+                qh = (qh + take) & (kDeferSlots - 1u);
+                qn -= take;
+                const uint32_t pm = take >= 32u ? kFull : (1u << take) - 1u;
+                stage_slabs(T, buf_s, uu, pm, lane);
+                cp_async_commit();
+                skeys[lane] = match_key(T, k, fixed_op<kKind>());
+                cp_async_wait<0>();
+                __syncwarp();
+                bool more = mine;
+                uint32_t rs = default_result(fixed_op<kKind>()), fd = 0u;
+                read_round<kKind, kKeyOnly>(T, buf, ballots, skeys, off, pm, more, uu, rs, fd);
+                round_done(more, rr);
+                if (mine && !more) {
+                    if (A.results) A.results[i] = rs;
+                    if (A.found) A.found[i] = (uint8_t)fd;
+                }
+                __syncwarp();
+                push(more, i, uu, k, rr);
+            }
+        }
         // (4) rotate the pipeline
         ck = nk; cv = nv; co = no; cb = nb;
         nk = mk; nv = mv; no = mo;

@@ -33,7 +33,7 @@ bool valid_config(const slab_config& c) {
     return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
            c.threads_per_block >= 32 && c.threads_per_block <= 1024 && c.threads_per_block % 32 == 0 &&
            c.blocks_per_sm >= 0 && c.blocks_per_sm <= 64 && c.iter_limit >= 1 && c.random_probes <= (1u << 20) &&
-           // staged kernels hold one 4 KB stage (plus 384 bytes) per warp
+           // staged kernels hold one 4 KB stage per warp, plus up to 1.4 KB of keys, ballots and waiting ops
            (c.variant != SLAB_VARIANT_STAGED ||
             c.threads_per_block / 32 * kStagedWordsPerWarp * 4 <= 227 * 1024);
 }
@@ -261,7 +261,7 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
         k<<<grid, tpb, 0, S(stream)>>>(T, a);
     } else {
         auto k = staged_kernel<kKind, kKeyOnly>;
-        const size_t smem = (size_t)wpb * kStagedWordsPerWarp * 4;
+        const size_t smem = (size_t)wpb * kWordsPerWarp<kKind> * 4;
         if ((int)smem > t->max_smem_optin) return SLAB_ERR_INVALID_ARG;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -414,3 +414,55 @@ def test_repeated_keys_in_one_batch_follow_a_serial_order(variant, key_only):
         assert tot["live"] == 6000 - 2000 + 3000 and tot["prefix_violations"] == 0
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("key_only", [False, True])
+def test_deferred_ops_cycle_through_long_lists(key_only):
+    """Staged kernels park ops that need another slab and serve them later, 32 at a
+    time. Lists of ~8 slabs and the smallest grid (one 32-thread block per SM, so
+    each warp serves many tiles) send every op round that ring several times and
+    wrap it over and over: inserts, replaces, searches, deletes and mixed batches
+    all agree with the oracle."""
+    n = 1 << 16
+    ks = W.KeyStream(41)
+    keys = ks.take(n)
+    a, b = W.hash_params(41)
+    per = 30 if key_only else 15
+    B = max(1, n // (8 * per))
+    p = Pair(B, a, b, key_only=key_only, n_hint=2 * n, threads_per_block=32, blocks_per_sm=1)
+    vals = None if key_only else W.values_for(keys)
+    try:
+        p.insert(keys, vals)
+        p.insert(keys[::2], None if key_only else vals[::2] + np.uint32(3))
+        p.search(np.concatenate([keys[::3], ks.take(n // 4)]))
+        p.delete(keys[1::4])
+        rng = np.random.default_rng(41)
+        live = np.setdiff1d(keys, keys[1::4])
+        for ratios in W.CONFIG3_RATIOS:
+            mb, live = W.mixed_batch(ks, live, n // 2, ratios, rng)
+            p.mixed(mb.ops, mb.keys, None if key_only else mb.values)
+        p.search(live[: n // 2])
+        tot = p.check_structure()
+        assert tot["slabs"] >= 4 * B
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+def test_growth_burst_in_a_tight_pool(variant):
+    """One batch whose ops all start together and pile onto 64 lists (~45 per
+    list, each list growing to 3-5 slabs): for a moment many more ops want a new
+    slab than the 1024-slab pool holds, though the table needs ~200. An op that
+    finds no free slab follows the slab another op linked meanwhile, so nothing
+    fails and the table matches the oracle."""
+    n = 64 * 45
+    keys = W.KeyStream(77).take(n)
+    a, b = W.hash_params(77)
+    p = Pair(64, a, b, pool_slabs=1024, variant=variant)
+    try:
+        p.insert(keys, W.values_for(keys))
+        tot = p.check_structure()
+        assert tot["pool_allocated"] < 400
+        p.search(keys)
+    finally:
+        p.close()
