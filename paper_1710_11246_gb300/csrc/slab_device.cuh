@@ -168,6 +168,8 @@ struct AllocCtx {
 };
 constexpr uint32_t kNoBlock = 0xFFFFFFFFu;
 constexpr uint32_t kAllocFailed = 0xFFFFFFFFu;
+static_assert(kAllocFailed == kEmptyKey, "an unlinked next pointer reads as a failed allocation");
+constexpr uint32_t kAllocRetry = 0xFFFFFFFEu;  // no slab this time; the pool may still have some
 
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     // murmur3 finalizer
@@ -191,13 +193,17 @@ __device__ __forceinline__ uint32_t resident_block(const TableView& T, uint32_t 
 }
 
 // Returns a pool address, or kAllocFailed once every block has been probed.
+// Each call may change the resident block random_probes + num_blocks times, so a
+// call that gives up has swept every block, and a warp that met a momentarily
+// full pool can allocate again later.
 // Must be called by all 32 lanes with warp-uniform control flow.
 __device__ __forceinline__ uint32_t warp_allocate(const TableView& T, AllocCtx& c, uint32_t warp_gid) {
     const uint32_t lane = lane_id();
     const uint32_t max_changes = T.random_probes + T.num_blocks;
+    const uint32_t start = c.changes;
     for (;;) {
         if (c.block == kNoBlock) {
-            if (c.changes >= max_changes) return kAllocFailed;
+            if (c.changes - start >= max_changes) return kAllocFailed;
             c.block = resident_block(T, warp_gid, c.changes);
             c.changes++;
             c.bitmap = ld_coherent(T.bitmaps + (uint64_t)c.block * 32 + lane);
@@ -223,22 +229,34 @@ __device__ __forceinline__ uint32_t warp_allocate(const TableView& T, AllocCtx& 
     }
 }
 
-// Batched allocation: every lane with `want` set receives its own pool address (or
-// kAllocFailed once every block has been probed). Lane i owns word i of the
-// resident block's bitmap, so in one round the k-th lane holding a free bit
-// claims it for the k-th requesting lane (lane order), and up to 32 claims are
-// in flight together instead of one per round trip. Losers of a bit race (the
-// atomic found the bit already set) refresh their word and go round again.
+// Batched allocation: every lane with `want` set receives its own pool address,
+// or kAllocFailed once every block has been probed (the budget is per call, as
+// above). Lane i owns word i of the resident block's bitmap, so in one round the
+// k-th lane holding a free bit claims it for the k-th requesting lane (lane
+// order), and up to 32 claims are in flight together instead of one per round
+// trip. Losers of a bit race (the atomic found the bit already set) refresh
+// their word and go round again.
+// With `yield`, a call that has already handed out slabs does not move on when
+// its block fills: the lanes still waiting get kAllocRetry. List growth uses
+// this so that a warp never holds new slabs while it searches the pool for
+// more; when many warps grow many lists at once, holding while searching can
+// keep the pool full until every search gives up.
 // Must be called by all 32 lanes with warp-uniform control flow.
-__device__ __forceinline__ uint32_t warp_allocate_many(const TableView& T, AllocCtx& c, uint32_t warp_gid,
-                                                       bool want) {
+__device__ __forceinline__ uint32_t warp_allocate_many(const TableView& T, AllocCtx& c, uint32_t warp_gid, bool want,
+                                                       bool yield = false) {
     const uint32_t lane = lane_id();
     const uint32_t below = (1u << lane) - 1u;
     const uint32_t max_changes = T.random_probes + T.num_blocks;
+    const uint32_t start = c.changes;
     uint32_t got = kAllocFailed;
-    for (uint32_t pending = __ballot_sync(kFull, want); pending;) {
+    const uint32_t wanted = __ballot_sync(kFull, want);
+    for (uint32_t pending = wanted; pending;) {
         if (c.block == kNoBlock) {
-            if (c.changes >= max_changes) break;
+            if (yield && pending != wanted) {  // some lanes hold new slabs already
+                if ((pending >> lane) & 1u) got = kAllocRetry;
+                break;
+            }
+            if (c.changes - start >= max_changes) break;
             c.block = resident_block(T, warp_gid, c.changes);
             c.changes++;
             c.bitmap = ld_coherent(T.bitmaps + (uint64_t)c.block * 32 + lane);

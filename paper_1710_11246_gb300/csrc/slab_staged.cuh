@@ -29,7 +29,8 @@
 // tile of such ops, 32 at a time, so one long list does not hold the whole warp
 // for another stage-and-match round. Insert and mixed batches serve each tile
 // to the end: their rounds also claim pairs and grow lists, and measured slower
-// when deferred.
+// when deferred. So do search and delete on tables much larger than L2 (the ones
+// whose slabs are pulled into L2 a tile ahead), where the ring measured slower.
 #pragma once
 #include "slab_device.cuh"
 #include "slab_wcws.cuh"
@@ -314,6 +315,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
         }
         // full lists grow by one slab each (SlabAlloc, Sec. 5)
         auto settle = [&](uint32_t nx) {
+            if (nx == kAllocRetry) return;  // still pending on the same slab: grow it in a later round
             if (nx == kAllocFailed) {
                 set_flag(T, kFlagOutOfSlabs);
                 pending = false;
@@ -470,6 +472,9 @@ __global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXN
         __syncwarp();
         const uint32_t idx = t * 32u + lane;
         if constexpr (kClaims<kKind>) {
+            serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb,
+                                        idx, idx < A.n);
+        } else if (T.prefetch_l2) {
             serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb,
                                         idx, idx < A.n);
         } else {

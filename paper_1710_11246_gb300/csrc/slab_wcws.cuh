@@ -78,7 +78,11 @@ __device__ __forceinline__ uint32_t default_result(uint32_t op) {
 __device__ __forceinline__ uint32_t grow_list(const TableView& T, AllocCtx& ac, uint32_t warp_gid,
                                               uint32_t* p_src_lane, int s) {
     uint32_t na = warp_allocate(T, ac, warp_gid);
-    if (na == kAllocFailed) return kAllocFailed;
+    if (na == kAllocFailed) {  // no slab left: follow a slab another op linked meanwhile, if any
+        uint32_t nx = kAllocFailed;
+        if ((int)lane_id() == s) nx = ld_coherent(p_src_lane + kAddressLane);
+        return __shfl_sync(kFull, nx, s);  // kEmptyKey (= kAllocFailed) while still unlinked
+    }
     uint32_t old = 0;
     if ((int)lane_id() == s) old = atomicCAS(p_src_lane + kAddressLane, kEmptyKey, na);
     old = __shfl_sync(kFull, old, s);
@@ -91,12 +95,18 @@ __device__ __forceinline__ uint32_t grow_list(const TableView& T, AllocCtx& ac, 
 // own full slab at `p` (the slab its op last read). The slabs for all such lanes
 // come from one batched allocation; each lane then issues its own 32-bit link
 // CAS on its slab's next pointer, and a lane that loses (another op linked first)
-// returns its slab and follows the winner's. Returns the slab to continue with,
-// or kAllocFailed where the pool had no slab left.
+// returns its slab and follows the winner's. Returns the slab to continue with;
+// kAllocRetry where the warp's batch got no slab this time (the op stays on its
+// slab and tries again in a later round); kAllocFailed where the pool had no
+// slab left. Either way a slab that another op linked meanwhile is followed.
 __device__ __forceinline__ uint32_t grow_lists(const TableView& T, AllocCtx& ac, uint32_t warp_gid, uint32_t* p,
                                                bool need) {
-    const uint32_t na = warp_allocate_many(T, ac, warp_gid, need);
-    if (!need || na == kAllocFailed) return kAllocFailed;
+    const uint32_t na = warp_allocate_many(T, ac, warp_gid, need, true);
+    if (!need) return kAllocFailed;
+    if (na >= kAllocRetry) {  // kAllocRetry or kAllocFailed
+        const uint32_t nx = ld_coherent(p + kAddressLane);
+        return nx != kEmptyKey ? nx : na;
+    }
     const uint32_t old = atomicCAS(p + kAddressLane, kEmptyKey, na);
     if (old == kEmptyKey) return na;
     deallocate(T, na);

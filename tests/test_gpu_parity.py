@@ -466,3 +466,32 @@ def test_growth_burst_in_a_tight_pool(variant):
         p.search(keys)
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("variant,key_only", [("staged", False), ("staged", True), ("direct", False)])
+def test_long_lists_in_a_table_larger_than_l2(variant, key_only):
+    """Search and delete on a table whose base slabs (2^20 x 128 B = 134 MB) are far
+    larger than half the L2, the case where those kernels restage an op's next slab
+    inside its tile (and pull slabs into L2 ahead) instead of parking the op. With
+    h(k) = k mod B (a = 1, b = 0) the keys bucket + j * B fill 1000 lists with 60
+    keys each (4 slabs in key-value mode, 2 in key-only mode); hits, misses and
+    deletes along the lists agree with the oracle. The one batch of inserts also
+    makes ~45 ops per list want a new slab at the same moment, in a pool about
+    three times the table's need."""
+    B = 1 << 20
+    j = np.arange(90, dtype=np.uint64)
+    keys = (np.arange(1000, dtype=np.uint64)[:, None] + j[None, :] * B).astype(np.uint32)
+    stored = keys[:, :60].ravel()
+    absent = keys[:, 60:].ravel()
+    rng = np.random.default_rng(7)
+    stored = stored[rng.permutation(len(stored))]
+    p = Pair(B, 1, 0, variant=variant, key_only=key_only, n_hint=len(stored))
+    try:
+        p.insert(stored, None if key_only else W.values_for(stored))
+        p.search(np.concatenate([stored[::2], absent[::3]]))
+        p.delete(stored[::3])
+        p.search(np.concatenate([stored, absent[::5]]))
+        tot = p.check_structure()
+        assert tot["slabs"] == B + (1000 if key_only else 3000)
+    finally:
+        p.close()
