@@ -363,11 +363,16 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
 
 // Register caps of the staged kernels: more resident warps hide more of each
 // tile's staging latency (all kernels) and claim round trip (insert, mixed).
+// Mixed batches run their three op kinds' actions side by side and do better
+// with a few more registers than bulk inserts.
 #ifndef SLAB_READ_MAXNREG
 #define SLAB_READ_MAXNREG 72
 #endif
 #ifndef SLAB_CLAIM_MAXNREG
 #define SLAB_CLAIM_MAXNREG 56
+#endif
+#ifndef SLAB_MIXED_MAXNREG
+#define SLAB_MIXED_MAXNREG 64
 #endif
 
 template <int kKind>
@@ -377,7 +382,8 @@ template <int kKind>
 constexpr uint32_t kWordsPerWarp = kClaims<kKind> ? kServeWordsPerWarp : kStagedWordsPerWarp;
 
 template <int kKind, bool kKeyOnly>
-__global__ void __maxnreg__(kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXNREG)
+__global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
+                                                : (kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXNREG))
     staged_kernel(TableView T, BatchArgs A) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
