@@ -78,7 +78,7 @@ typedef struct slab_config {
     int32_t threads_per_block; /* multiple of 32, 32..1024 */
     int32_t blocks_per_sm;     /* resident blocks per SM used to size the persistent grid; 0 = occupancy maximum */
     uint32_t iter_limit;       /* cap on slab reads and retries of one op; reaching it ends the op with SLAB_FLAG_ITER_LIMIT */
-    uint32_t random_probes;    /* SlabAlloc resident changes drawn by hash before a linear sweep of all blocks */
+    uint32_t random_probes;    /* per allocation: SlabAlloc block changes drawn by hash before a sweep of all blocks */
 } slab_config;
 
 /* Geometry of one table (read-only). */
