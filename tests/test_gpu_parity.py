@@ -205,6 +205,48 @@ def test_iteration_cap_ends_ops_with_a_status(variant):
         p.close()
 
 
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("key_only", [False, True])
+def test_iteration_cap_counts_slab_reads_across_the_ring(variant, key_only):
+    """One bucket filled one slab per batch (five slabs). With a cap of two slab reads
+    per op, searches and deletes of keys in the first two slabs finish (in the staged
+    kernels the second slab is read when the op's turn in the warp's ring comes) and
+    the others stop with ITER_LIMIT and report not found; with the cap lifted, the
+    table agrees with the oracle."""
+    per = 30 if key_only else 15
+    keys = W.KeyStream(91).take(5 * per)
+    vals = None if key_only else W.values_for(keys)
+    p = Pair(1, 5, 6, variant=variant, key_only=key_only, n_hint=5 * per)
+    try:
+        for j in range(5):
+            p.insert(keys[j * per:(j + 1) * per], None if key_only else vals[j * per:(j + 1) * per])
+        tot = p.check_structure()
+        assert tot["slabs"] == 5
+        cap = sh.slab_get_config(p.g.handle).iter_limit
+        p.g.configure(iter_limit=2)
+        fd = torch.full((len(keys),), 7, dtype=torch.uint8, device="cuda")
+        got = host(p.g.search(dev(keys), found=fd))
+        rc, flags = p.g.status()
+        assert rc == sh.SLAB_ERR_ITER_LIMIT and flags == sh.SLAB_FLAG_ITER_LIMIT
+        f = u8(fd)
+        assert (f[:2 * per] == 1).all() and (f[2 * per:] == 0).all()
+        if not key_only:
+            assert (got[:2 * per] == vals[:2 * per]).all()
+        dk = keys[::2]
+        fd = torch.full((len(dk),), 7, dtype=torch.uint8, device="cuda")
+        p.g.delete(dev(dk), fd)
+        rc, flags = p.g.status()
+        assert flags & sh.SLAB_FLAG_ITER_LIMIT
+        in_first_two = np.isin(dk, keys[:2 * per])
+        assert (u8(fd) == in_first_two).all()
+        p.o.delete(dk[in_first_two])
+        p.g.configure(iter_limit=cap)
+        p.search(keys)
+        p.check_structure()
+    finally:
+        p.close()
+
+
 @pytest.mark.parametrize("variant,tpb,bps", [("staged", 32, 1), ("staged", 128, 2), ("staged", 256, 0),
                                              ("staged", 512, 1), ("staged", 768, 1), ("direct", 32, 1),
                                              ("direct", 128, 2), ("direct", 512, 0), ("direct", 1024, 1)])
