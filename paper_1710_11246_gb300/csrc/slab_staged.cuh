@@ -17,8 +17,8 @@
 // of a tile are in flight together and their results are checked once. A claim
 // that lost its race tries the following pair of the same slab at once; ops that
 // must follow a next pointer, or that ran off their slab, restage just their
-// slabs and go round again; a full list grows through SlabAlloc exactly as in the
-// paper.
+// slabs and go round again; a full list grows through SlabAlloc (Sec. 5), by one
+// batched allocation for all of a bulk-insert tile's full lists.
 //
 // Staging just before serving (rather than a tile ahead into a second buffer)
 // keeps one 4 KB stage per warp, which leaves room for more resident warps, and

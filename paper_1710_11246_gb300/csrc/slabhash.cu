@@ -89,15 +89,19 @@ __global__ void reset_kernel(uint4* base, uint64_t base16, uint4* pool, uint32_t
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint4 ones = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
     for (uint64_t i = tid; i < base16; i += stride) base[i] = ones;
-    for (uint64_t w = tid; w < words; w += stride) {
-        uint32_t bits = bitmaps[w];
-        if (!bits) continue;
-        bitmaps[w] = 0;
-        const uint64_t first_unit = (w >> 5) * kUnitsPerBlock + (w & 31u) * 32u;
-        for (; bits; bits &= bits - 1u) {
-            uint4* slab = pool + (first_unit + (uint64_t)(__ffs(bits) - 1)) * 8u;
+    // A warp per bitmap word: lanes 8g..8g+7 write slab 4j + g of the word's 32
+    // (16 bytes each), so one store instruction refills four slabs.
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint64_t w = tid >> 5; w < words; w += stride >> 5) {
+        const uint32_t bits = bitmaps[w];  // the same word in every lane
+        if (!bits) continue;                // warp-uniform
+        __syncwarp();
+        if (lane == 0) bitmaps[w] = 0;
+        uint4* first = pool + ((w >> 5) * kUnitsPerBlock + (w & 31u) * 32u) * 8u;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) slab[c] = ones;
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t slab = 4u * j + (lane >> 3);
+            if ((bits >> slab) & 1u) first[slab * 8u + (lane & 7u)] = ones;
         }
     }
     if (tid == 0) misc[0] = 0;
