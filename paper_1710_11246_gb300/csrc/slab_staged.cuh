@@ -95,38 +95,48 @@ __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, 
     }
 }
 
-// One WCWS round (Fig. "alg:search") of a search or delete batch for the ops of
-// the lanes in `pend`, each of whose current slab (unified index u) is staged in
-// slot `lane` of `buf`, with keys in `skeys`: the warp takes the queued ops in
-// lane order and finds each one's matching lanes by ballot, then every source
-// lane acts on its ballot (reads the value, or writes the tombstone). On return
-// an op that is done has its result in res / fnd and pending cleared; one that
-// goes on has u set to its list's next slab.
-template <int kKind, bool kKeyOnly>
-__device__ __forceinline__ void read_round(const TableView& T, const uint32_t* buf, uint32_t* ballots,
-                                           const uint32_t* skeys, const uint32_t (&off)[8], uint32_t pend,
-                                           bool& pending, uint32_t& u, uint32_t& res, uint32_t& fnd) {
-    static_assert(kKind == kKindSearch || kKind == kKindDelete, "claims serve whole tiles (serve_tile)");
-    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+// The WCWS match of one round (Fig. "alg:search"): the warp takes the queued ops
+// (bits of `pend`) in lane order; for each op s it compares word `lane` of the
+// op's staged slab (slot s) with the op's key from the shared copy of the tile's
+// keys (an insert also with EMPTY, a mixed op also with its alternate key) and
+// lane 0 stores the ballot in ballots[s]. Three forms of the same loop: all 32
+// ops queued (`full`: keys read and ballots stored four at a time, no
+// branches), `wide` (unrolled over the 32 slots, one predicate per op) and a loop
+// over the set bits (few ops).
+template <int kKind>
+__device__ __forceinline__ void wcws_ballots(const uint32_t* buf, uint32_t* ballots, const uint32_t* skeys,
+                                             const uint32_t* salts, const uint32_t (&off)[8], uint32_t pend,
+                                             bool full, bool wide) {
     const uint32_t lane = lane_id();
+    auto match = [&](uint32_t data, uint32_t skey, uint32_t salt) {
+        bool pred;
+        if constexpr (kKind == kKindInsert) {
+            pred = data == skey || data == kEmptyKey;
+        } else if constexpr (kKind == kKindMixed) {
+            pred = data == skey || data == salt;
+        } else {
+            pred = data == skey;
+        }
+        return __ballot_sync(kFull, pred);
+    };
     auto step = [&](uint32_t s, uint32_t data) {
-        const uint32_t mm = __ballot_sync(kFull, data == skeys[s]);
+        const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? salts[s] : 0u);
         if (lane == 0) ballots[s] = mm;
     };
-    if (pend == kFull) {
-        // four ops per key load and per ballot store, no branches
+    if (full) {
 #pragma unroll
         for (uint32_t g = 0; g < 8; ++g) {
             const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
+            const uint4 a4 = kKind == kKindMixed ? *reinterpret_cast<const uint4*>(salts + 4u * g) : k4;
             const uint32_t s0 = 4u * g;
             uint4 b4;
-            b4.x = __ballot_sync(kFull, buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]] == k4.x);
-            b4.y = __ballot_sync(kFull, buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]] == k4.y);
-            b4.z = __ballot_sync(kFull, buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]] == k4.z);
-            b4.w = __ballot_sync(kFull, buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]] == k4.w);
+            b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, a4.x);
+            b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, a4.y);
+            b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, a4.z);
+            b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, a4.w);
             if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
         }
-    } else if (__popc(pend) > 8) {
+    } else if (wide) {
 #pragma unroll
         for (uint32_t s = 0; s < 32; ++s)
             if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
@@ -136,6 +146,22 @@ __device__ __forceinline__ void read_round(const TableView& T, const uint32_t* b
             step(s, buf[swz(s, lane)]);
         }
     }
+}
+
+// One WCWS round (Fig. "alg:search") of a search or delete batch for the ops of
+// the lanes in `pend`, each of whose current slab (unified index u) is staged in
+// slot `lane` of `buf`, with keys in `skeys`: the ballots of wcws_ballots, then
+// every source lane acts on its ballot (reads the value, or writes the tombstone). On return
+// an op that is done has its result in res / fnd and pending cleared; one that
+// goes on has u set to its list's next slab.
+template <int kKind, bool kKeyOnly>
+__device__ __forceinline__ void read_round(const TableView& T, const uint32_t* buf, uint32_t* ballots,
+                                           const uint32_t* skeys, const uint32_t (&off)[8], uint32_t pend,
+                                           bool& pending, uint32_t& u, uint32_t& res, uint32_t& fnd) {
+    static_assert(kKind == kKindSearch || kKind == kKindDelete, "claims serve whole tiles (serve_tile)");
+    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    const uint32_t lane = lane_id();
+    wcws_ballots<kKind>(buf, ballots, skeys, skeys, off, pend, pend == kFull, __popc(pend) > 8);
     __syncwarp();
     // the source lanes act on their ballots (Sec. 4.3)
     const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
@@ -193,46 +219,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
             __syncwarp();
         }
         // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
-        // The source key is broadcast from the shared copy of the tile's keys.
-        auto match = [&](uint32_t data, uint32_t skey, uint32_t salt) {
-            bool pred;
-            if constexpr (kKind == kKindInsert) {
-                pred = data == skey || data == kEmptyKey;
-            } else if constexpr (kKind == kKindMixed) {
-                pred = data == skey || data == salt;
-            } else {
-                pred = data == skey;
-            }
-            return __ballot_sync(kFull, pred);
-        };
-        auto step = [&](uint32_t s, uint32_t data) {
-            const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? salts[s] : 0u);
-            if (lane == 0) ballots[s] = mm;
-        };
-        if (first && pend == kFull) {
-            // the common case: four ops per key load and per ballot store, no branches
-#pragma unroll
-            for (uint32_t g = 0; g < 8; ++g) {
-                const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
-                const uint4 a4 = kKind == kKindMixed ? *reinterpret_cast<const uint4*>(salts + 4u * g) : k4;
-                const uint32_t s0 = 4u * g;
-                uint4 b4;
-                b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, a4.x);
-                b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, a4.y);
-                b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, a4.z);
-                b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, a4.w);
-                if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
-            }
-        } else if (first) {
-#pragma unroll
-            for (uint32_t s = 0; s < 32; ++s)
-                if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
-        } else {
-            for (uint32_t q = pend; q; q &= q - 1u) {
-                const uint32_t s = (uint32_t)(__ffs(q) - 1);
-                step(s, buf[swz(s, lane)]);
-            }
-        }
+        wcws_ballots<kKind>(buf, ballots, skeys, salts, off, pend, first && pend == kFull, first);
         __syncwarp();
 
         // the source lanes act on their ballots (Sec. 4.3)
