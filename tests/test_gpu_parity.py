@@ -537,3 +537,27 @@ def test_long_lists_in_a_table_larger_than_l2(variant, key_only):
         assert tot["slabs"] == B + (1000 if key_only else 3000)
     finally:
         p.close()
+
+
+def test_full_size_step_matches_the_oracle():
+    """The benchmark's step at full size, in its launch configuration (staged
+    kernels, default block size and occupancy): 2^22 pairs built at beta 0.6, 2^22
+    searches at 50 % hit, 2^20 deletes, then 2^20 mixed ops at (0.2, 0.2, 0.6).
+    The oracle runs the same 10.5 M ops; every result, found flag, per-bucket slot
+    and slab count and the exported table agree element by element."""
+    w = W.config2(0.6, 0.5, seed=0)
+    ks = W.KeyStream(0)
+    ks.take(len(w.keys) + (len(w.search.keys) - int(round(len(w.search.keys) * 0.5))))
+    rng = np.random.default_rng([0, 0x3333])
+    live = np.setdiff1d(w.keys, w.delete_keys, assume_unique=True)
+    mb, _ = W.mixed_batch(ks, live, 1 << 20, (0.2, 0.2, 0.6), rng)
+    p = Pair(w.num_buckets, w.hash_a, w.hash_b, pool_slabs=1 << 20)
+    try:
+        assert p.insert(w.keys, w.values).sum() == 0
+        _, found = p.search(w.search.keys)
+        assert (found.astype(bool) == w.search.present).all()
+        assert p.delete(w.delete_keys).all()
+        p.mixed(mb.ops, mb.keys, mb.values)
+        p.check_structure()
+    finally:
+        p.close()
