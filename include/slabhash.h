@@ -144,7 +144,11 @@ int slab_set_config(slab_table *t, const slab_config *cfg);
  * (Sec. 3.2 "Insertion", Sec. 4.3.2): if k is present its value is replaced,
  * otherwise the pair takes the first empty slot of its list, and a full list
  * grows by one SlabAlloc slab linked by a 32-bit CAS on the tail's next
- * pointer. Deleted slots are not reused, so keys stay unique (Sec. 3.2).
+ * pointer. Deleted slots are not reused, so keys stay unique (Sec. 3.2). An
+ * insert that finds no free slab while other ops of the batch hold new slabs
+ * not yet linked tries again in a later round; only when a search of every
+ * memory block finds none does it end with SLAB_FLAG_OUT_OF_SLABS (the op's
+ * found byte is then 0 and the pair is not stored; slab_status reports it).
  * d_keys, d_values: n uint32 each (d_values ignored in key-only mode, may be
  * NULL there). d_found (nullable): n bytes, 1 if the key was already present
  * (its value replaced), else 0.
