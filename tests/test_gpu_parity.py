@@ -561,3 +561,45 @@ def test_full_size_step_matches_the_oracle():
         p.check_structure()
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("beta", [0.2, 2.0])
+def test_full_size_betas_and_hit_rates_match_the_oracle(beta):
+    """2^22 pairs at the smallest and largest mean fill of the bulk sweep (beta 0.2:
+    1.4 M one-slab lists; beta 2.0: 2.45 slabs per list, so many searches and
+    deletes go on through the ring), 2^22 searches at 100 % and at 0 % hit, 2^20
+    deletes: every output and the final table agree with the oracle."""
+    w1 = W.config2(beta, 1.0, seed=0)
+    w0 = W.config2(beta, 0.0, seed=0)
+    assert (w1.keys == w0.keys).all()
+    p = Pair(w1.num_buckets, w1.hash_a, w1.hash_b, pool_slabs=1 << 21)
+    try:
+        assert p.insert(w1.keys, w1.values).sum() == 0
+        _, f1 = p.search(w1.search.keys)
+        _, f0 = p.search(w0.search.keys)
+        assert f1.all() and not f0.any()
+        assert p.delete(w1.delete_keys).all()
+        p.search(w1.search.keys[: 1 << 20])
+        p.check_structure()
+    finally:
+        p.close()
+
+
+def test_slab_alloc_full_size():
+    """The SlabAlloc microbenchmark's size (Sec. 5): 2^24 single-slab allocations
+    from a pool of 2^25 units in one launch give 2^24 distinct valid addresses that
+    the bitmaps mark exactly; freeing them all clears every bit."""
+    from oracle import check_alloc
+    t = sh.SlabHash(8, 3, 4, pool_slabs=1 << 25)
+    try:
+        n = 1 << 24
+        addrs = torch.empty(n, dtype=torch.int32, device="cuda")
+        sh.slab_alloc_batch(t.handle, addrs)
+        rc, flags = t.status()
+        assert rc == sh.SLAB_OK, flags
+        a = host(addrs)
+        assert check_alloc(a, host(t.bitmaps()), t.info.num_memory_blocks) == (0, 0)
+        sh.slab_free_batch(t.handle, addrs)
+        assert (host(t.bitmaps()) == 0).all()
+    finally:
+        t.close()
