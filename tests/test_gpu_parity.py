@@ -603,3 +603,26 @@ def test_slab_alloc_full_size():
         assert (host(t.bitmaps()) == 0).all()
     finally:
         t.close()
+
+
+def test_full_size_concurrent_batches_match_the_oracle():
+    """The concurrent benchmark's sizes (Sec. 6.3): 2^22 pairs preloaded at beta 0.6,
+    then batches of 2^20 mixed ops at each of (0.5, 0.5, 0), (0.2, 0.2, 0.6) and
+    (0.05, 0.05, 0.9), three batches per ratio here (the benchmark runs 64): every
+    result and found flag and the final table agree with the oracle."""
+    w = W.config2(0.6, 0.5, seed=3)
+    ks = W.KeyStream(3)
+    ks.take(len(w.keys) + len(w.search.keys))
+    rng = np.random.default_rng(3)
+    p = Pair(w.num_buckets, w.hash_a, w.hash_b, pool_slabs=1 << 21)
+    try:
+        assert p.insert(w.keys, w.values).sum() == 0
+        live = w.keys
+        for ratios in W.CONFIG3_RATIOS:
+            for _ in range(3):
+                mb, live = W.mixed_batch(ks, live, 1 << 20, ratios, rng)
+                p.mixed(mb.ops, mb.keys, mb.values)
+        p.search(live[: 1 << 20])
+        p.check_structure()
+    finally:
+        p.close()
