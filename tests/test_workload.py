@@ -50,3 +50,33 @@ def test_serving_trace_rate_changes_arrivals_only():
     c = W.serving_trace(1 << 12, 4000, 1e4, max_size=4, seed=2)
     gaps = np.diff(np.concatenate([[0], c.arrival_ns.astype(np.int64)]))
     assert abs(gaps.mean() / 1e5 - 1) < 0.05
+
+
+def test_mixed_batch_keys_once_each_and_the_live_set_follows():
+    """Concurrent-benchmark batches (Sec. 6.3): every key appears in at most one op of
+    a batch, so every outcome is fixed; inserts take fresh keys, deletes take live
+    keys, half of the searches hit live keys that the batch does not delete, the
+    op counts follow the ratios, no key is a sentinel, and the returned live set
+    is the old one minus the deletes plus the inserts."""
+    for ratios in W.CONFIG3_RATIOS:
+        ks = W.KeyStream(11)
+        live = ks.take(50000)
+        rng = np.random.default_rng(11)
+        for _ in range(3):
+            n = 20000
+            mb, new_live = W.mixed_batch(ks, live, n, ratios, rng)
+            assert len(mb.keys) == len(mb.ops) == len(mb.values) == n
+            assert len(np.unique(mb.keys)) == n
+            assert (mb.keys < 0xFFFFFFFE).all()
+            ins = mb.keys[mb.ops == W.OP_INSERT]
+            dels = mb.keys[mb.ops == W.OP_DELETE]
+            srch = mb.keys[mb.ops == W.OP_SEARCH]
+            assert len(ins) == round(n * ratios[0]) and len(dels) == round(n * ratios[1])
+            assert not np.isin(ins, live).any() and np.isin(dels, live).all()
+            hits = np.isin(srch, live)
+            assert hits.sum() == len(srch) // 2 and not np.isin(srch[hits], dels).any()
+            assert (mb.values[mb.ops == W.OP_INSERT] == W.values_for(ins)).all()
+            assert (mb.values[mb.ops != W.OP_INSERT] == 0).all()
+            want = np.union1d(np.setdiff1d(live, dels), ins)
+            assert len(new_live) == len(want) and (np.sort(new_live) == want).all()
+            live = new_live
