@@ -80,3 +80,20 @@ def test_mixed_batch_keys_once_each_and_the_live_set_follows():
             want = np.union1d(np.setdiff1d(live, dels), ins)
             assert len(new_live) == len(want) and (np.sort(new_live) == want).all()
             live = new_live
+
+
+def test_bulk_workload_shapes():
+    """The bulk benchmark's inputs (Sec. 6.1) at the small size: distinct
+    non-sentinel keys, value = key XOR the fixed constant, B = ceil(n / (15 beta)),
+    searches whose `present` flags are exactly membership in the stored keys at
+    the stated hit rate, and distinct deletes of stored keys."""
+    w = W.config1()
+    n = len(w.keys)
+    assert n == 1 << 16 and len(np.unique(w.keys)) == n and (w.keys < 0xFFFFFFFE).all()
+    assert (w.values == (w.keys ^ np.uint32(0x9E3779B9))).all()
+    assert w.num_buckets == int(np.ceil(n / (15 * 0.6))) == 7282
+    q = w.search.keys
+    assert len(q) == 1 << 16 and (w.search.present == np.isin(q, w.keys)).all()
+    assert w.search.present.sum() == len(q) // 2 and len(np.unique(q)) == len(q)
+    d = w.delete_keys
+    assert len(d) == 1 << 14 and len(np.unique(d)) == len(d) and np.isin(d, w.keys).all()
