@@ -292,24 +292,30 @@ int slab_copy_bitmaps(const slab_table *t, uint32_t *d_dst, uint64_t n_words, vo
 /*
  * Slab-list length histogram and chain totals, with no device allocation at all.
  * The paper has no counterpart: this is a library service for callers that
- * cannot call cudaMalloc at the moment they need table statistics - a thread in
- * the middle of CUDA stream capture (an allocation there is illegal or breaks
- * the capture), a serving loop whose device memory is fully reserved by another
- * allocator (a fresh cudaMalloc would fail or fragment that pool), or a
- * latency-critical path that cannot afford the device synchronization an
- * allocation may cause. It walks every list like slab_stats and counts buckets
- * by slab count: h_hist[i] (n_bins uint64, host) = buckets whose list has i + 1
- * slabs, the last bin taking every longer list. h_totals (nullable, 6 uint64,
- * host) = the slab_stats totals. 1 <= n_bins <= 1024; a larger n_bins, or a
- * current device other than the table's, returns SLAB_ERR_INVALID_ARG.
+ * cannot call cudaMalloc at the moment they need table statistics - a serving
+ * loop whose device memory is fully reserved by another allocator (a fresh
+ * cudaMalloc would fail or fragment that pool), or a latency-critical path that
+ * cannot afford the device synchronization an allocation may cause. It walks
+ * every list like slab_stats and counts buckets by slab count: h_hist[i]
+ * (n_bins uint64, host) = buckets whose list has i + 1 slabs, the last bin
+ * taking every longer list. h_totals (nullable, 6 uint64, host) = the
+ * slab_stats totals. 1 <= n_bins <= 1024; a larger n_bins, or a current device
+ * other than the table's, returns SLAB_ERR_INVALID_ARG.
+ * It must be called outside CUDA stream capture: it ends by copying into host
+ * memory and synchronizing `stream`, which a capturing stream does not allow,
+ * so on a capturing stream (or on the legacy stream while another stream
+ * captures) it returns SLAB_ERR_INVALID_ARG before enqueueing anything and the
+ * capture stays valid.
  * Scratch: a fixed device array of 1032 uint64 (about 8 KiB) compiled into the
  * library; every GPU that loads the library holds it until the process exits.
- * The first call on a device resolves the array's device address (once per
- * device, with that device current), so make the first call on each device
- * before any stream capture. The array is shared by all calls and keeps the last
- * call's counts: each call clears it on `stream` first, and calls that overlap
- * on the GPU (other streams, other host threads) race on it. Synchronizes
- * `stream`. Calls no cudaMalloc, cudaFree or other allocating routine.
+ * slab_create resolves the array's device address on the table's device and
+ * loads this call's kernels, so the call itself loads nothing on a device where
+ * a table was created since the last device reset (a table of a group, on a
+ * device where slab_create never ran, resolves the address on its first call).
+ * The array is shared by all calls and keeps the last call's counts: each call
+ * clears it on `stream` first, and calls that overlap on the GPU (other streams,
+ * other host threads) race on it. Synchronizes `stream`. Calls no cudaMalloc,
+ * cudaFree or other allocating routine.
  */
 int slab_chain_histogram_noalloc(slab_table *t, uint32_t n_bins, uint64_t *h_hist, uint64_t *h_totals,
                                  void *stream);
@@ -523,6 +529,18 @@ const char *slab_error_string(int rc);
 int slab_probe_random_lines(const uint32_t *d_buf, uint64_t footprint_lines, uint64_t n_reads,
                             uint32_t seed, int lines_in_flight, int threads_per_block,
                             uint32_t *d_sink, void *stream);
+/* slab_probe_random_lines_v4: the same n_reads random whole-line reads, each line
+ * read the way the staged kernels move slabs, as eight 16-byte pieces by 8
+ * lanes, so one warp instruction covers four lines. form 0: ld.global.cg.v4
+ * into registers, lines_in_flight in {4, 8, 16, 32} lines issued per warp
+ * before any is consumed. form 1: cp.async.cg 16-byte copies into a 4 KiB
+ * shared-memory stage of 32 lines per warp, lines_in_flight 32 (one stage,
+ * issued, waited for, consumed) or 64 (two stages: the next 32 lines are issued
+ * before this round is consumed). Same buffer, sink and error rules as above;
+ * an unsupported form or count returns SLAB_ERR_INVALID_ARG. */
+int slab_probe_random_lines_v4(const uint32_t *d_buf, uint64_t footprint_lines, uint64_t n_reads,
+                               uint32_t seed, int form, int lines_in_flight, int threads_per_block,
+                               uint32_t *d_sink, void *stream);
 int slab_probe_random_cas(unsigned long long *d_buf, uint64_t footprint_lines, uint64_t n_ops,
                           uint32_t seed, int ops_in_flight, int threads_per_block, void *stream);
 /* slab_probe_random_or: n_ops 32-bit atomicOr operations, each setting one random

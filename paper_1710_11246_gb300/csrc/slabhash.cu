@@ -29,6 +29,11 @@ using slab_host::S;
 using slab_host::util_grid;
 using slab_host::view;
 
+// Set-up of the no-allocation statistics call on device `dev` (defined with it at
+// the end of this file): resolves its scratch array's device address and loads
+// its kernels. Returns false on a CUDA error.
+bool noalloc_setup(int dev);
+
 bool valid_config(const slab_config& c) {
     return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
            c.threads_per_block >= 32 && c.threads_per_block <= 1024 && c.threads_per_block % 32 == 0 &&
@@ -384,7 +389,7 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     t->cfg.random_probes = kDefaultRandomProbes;
     if (cudaMemset(t->d_misc, 0, 128) != cudaSuccess || cudaMemset(t->d_model, 0, model_bytes) != cudaSuccess ||
         fill_table(t, nullptr) != SLAB_OK ||
-        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaDeviceSynchronize() != cudaSuccess || !noalloc_setup(t->device)) {
         slab_destroy(t);
         return SLAB_ERR_CUDA;
     }
@@ -622,14 +627,23 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocTo
 std::mutex g_noalloc_mutex;
 unsigned long long* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on `dev`, resolved once per device with
-// that device current. The host-side name of the array is only a stand-in and
-// must never be passed to a kernel.
-unsigned long long* noalloc_scratch(int dev) {
+template <bool kKeyOnly>
+__global__ void chain_histogram_kernel(TableView T, uint32_t n_bins, unsigned long long* acc);
+
+// Device address of g_noalloc_scratch on `dev`, resolved with that device
+// current. The host-side name of the array is only a stand-in and must never be
+// passed to a kernel. `refresh` resolves it again even if it is cached: every
+// slab_create does so (allocation is allowed there, and loading the module may
+// allocate), which also replaces an address left over from before a device
+// reset, since every table in use was created after the last reset.
+unsigned long long* noalloc_scratch(int dev, bool refresh) {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    if (refresh || !g_noalloc_ptr[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            g_noalloc_ptr[dev] = nullptr;
+            return nullptr;
+        }
         g_noalloc_ptr[dev] = static_cast<unsigned long long*>(p);
     }
     return g_noalloc_ptr[dev];
@@ -686,15 +700,36 @@ __global__ void chain_histogram_kernel(TableView T, uint32_t n_bins, unsigned lo
         if (hist[i]) atomicAdd(acc + kNoAllocTotals + i, (unsigned long long)hist[i]);
 }
 
+bool noalloc_setup(int dev) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return true;  // such devices are refused by the call itself
+    // load the call's kernels now, so that its first launch does not
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, chain_histogram_kernel<false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, chain_histogram_kernel<true>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, popcount_kernel) != cudaSuccess)
+        return false;
+    return noalloc_scratch(dev, true) != nullptr;
+}
+
 }  // namespace
 
 extern "C" int slab_chain_histogram_noalloc(slab_table* t, uint32_t n_bins, uint64_t* h_hist, uint64_t* h_totals,
                                             void* stream) {
     if (!t || !h_hist || n_bins == 0 || n_bins > kNoAllocMaxBins) return SLAB_ERR_INVALID_ARG;
+    // the call ends with copies into host memory and a stream synchronization,
+    // neither of which a capturing stream allows: refuse before enqueueing anything
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t qe = cudaStreamIsCapturing(S(stream), &cap);
+    if (qe == cudaErrorStreamCaptureImplicit) {  // the legacy stream while another stream captures
+        cudaGetLastError();
+        return SLAB_ERR_INVALID_ARG;
+    }
+    if (qe != cudaSuccess) return SLAB_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return SLAB_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return SLAB_ERR_CUDA;
     if (dev != t->device || dev < 0 || dev >= kNoAllocMaxDevices) return SLAB_ERR_INVALID_ARG;
-    unsigned long long* acc = noalloc_scratch(dev);
+    unsigned long long* acc = noalloc_scratch(dev, false);
     if (!acc) return SLAB_ERR_CUDA;
     // every call starts from zeroed counters; the array keeps the previous call's values
     if (cudaMemsetAsync(acc, 0, (kNoAllocTotals + n_bins) * sizeof(unsigned long long), S(stream)) != cudaSuccess)

@@ -37,7 +37,7 @@ EXPORTED = [
     "slab_server_create", "slab_server_destroy", "slab_server_submit", "slab_server_collect",
     "slab_server_get_stats", "slab_server_run",
     "slab_set_multiset", "slab_search_all_batch", "slab_delete_all_batch", "slab_flush", "slab_grow_pool",
-    "slab_hash_params", "slab_create_seeded", "slab_probe_random_or",
+    "slab_hash_params", "slab_create_seeded", "slab_probe_random_or", "slab_probe_random_lines_v4",
 ]
 SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY, SLAB_SERVER_GROW_POOL = 64, 1 << 24, 1, 2
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
@@ -114,6 +114,7 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_copy_bitmaps": (i32, [vp, vp, u64, vp]),
             "slab_error_string": (C.c_char_p, [i32]),
             "slab_probe_random_lines": (i32, [vp, u64, u64, u32, i32, i32, vp, vp]),
+            "slab_probe_random_lines_v4": (i32, [vp, u64, u64, u32, i32, i32, i32, vp, vp]),
             "slab_probe_random_cas": (i32, [vp, u64, u64, u32, i32, i32, vp]),
             "slab_chain_histogram_noalloc": (i32, [vp, u32, C.POINTER(u64), C.POINTER(u64), vp]),
             "slab_learn_buckets": (i32, [vp, vp, u32, u32, i32, C.POINTER(SlabLearnReport), vp]),
@@ -304,6 +305,13 @@ def slab_probe_random_lines(buf, footprint_lines: int, n_reads: int, seed: int, 
     _check(load_library().slab_probe_random_lines(
         _dptr(buf, 4, footprint_lines * 32, "buf"), footprint_lines, n_reads, seed, lines_in_flight,
         threads_per_block, _dptr(sink, 4, 1, "sink"), _stream(stream)), "slab_probe_random_lines")
+
+
+def slab_probe_random_lines_v4(buf, footprint_lines: int, n_reads: int, seed: int, form: int, lines_in_flight: int,
+                               threads_per_block: int, sink, stream=None) -> None:
+    _check(load_library().slab_probe_random_lines_v4(
+        _dptr(buf, 4, footprint_lines * 32, "buf"), footprint_lines, n_reads, seed, form, lines_in_flight,
+        threads_per_block, _dptr(sink, 4, 1, "sink"), _stream(stream)), "slab_probe_random_lines_v4")
 
 
 def slab_probe_random_cas(buf, footprint_lines: int, n_ops: int, seed: int, ops_in_flight: int,

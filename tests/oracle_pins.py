@@ -433,6 +433,24 @@ def pin_multiset_golden(lib):
             raise AssertionError(op)
 
 
+def pin_multiset_insert_lines(lib):
+    """Slab reads of multiset INSERT and DELETE, hand-derived on one bucket
+    (tests/golden/multiset_insert_lines.txt): an insert that fills a hole reads up
+    to the hole's slab, one that appends up to the tail slot's slab."""
+    t = _multiset_table(1, lib)
+    for row in _rows("multiset_insert_lines.txt"):
+        op, args = row[0], row[1:]
+        want = int(args[args.index("->") + 1])
+        before = t.lines
+        if op == "insert":
+            t.insert([int(args[0])], [int(args[1])])
+        elif op == "delete":
+            assert int(t.delete([int(args[0])])[0]) == 1
+        else:
+            raise AssertionError(op)
+        assert t.lines - before == want, (row, t.lines - before)
+
+
 def pin_multiset_bruteforce(lib):
     """Random INSERT / DELETE / DELETEALL / SEARCH(ALL) sequences over a tiny key
     universe agree with the flat multiset model. Every instance of a key carries the

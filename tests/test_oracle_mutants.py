@@ -23,6 +23,9 @@ MUTANTS = {
     "hash_wrong_prime": ("#define OR_PRIME 4294967291ull", "#define OR_PRIME 4294967279ull"),
     "hash_skips_mod_p": ("(x % OR_PRIME) % num_buckets", "x % num_buckets"),
     "tombstone_matches": ("if (bk->s[s].live == OR_LIVE && bk->s[s].key == key)", "if (bk->s[s].key == key)"),
+    "multiset_insert_lines_to_tail": (
+        "while (s < bk->len && bk->s[s].live != OR_HOLE) s++;\n    if (lines) *lines += (uint64_t)s / t->M + 1;",
+        "while (s < bk->len && bk->s[s].live != OR_HOLE) s++;\n    if (lines) *lines += (uint64_t)bk->len / t->M + 1;"),
     "multiset_insert_appends": ("while (s < bk->len && bk->s[s].live != OR_HOLE) s++;", "s = bk->len;"),
     "multiset_delete_tombstones": ("bk->s[s].live = t->multiset ? OR_HOLE : OR_TOMB;", "bk->s[s].live = OR_TOMB;"),
     "delete_all_first_only": ("                    kill(t, bk, s);\n                    c++;\n",
