@@ -44,6 +44,8 @@ def load_oracle(path: str | None = None):
             u32p, u8p, u64p = C.POINTER(C.c_uint32), C.POINTER(C.c_uint8), C.POINTER(C.c_uint64)
             lib.oracle_create.restype = C.c_void_p
             lib.oracle_create.argtypes = [C.c_uint32, C.c_int, C.c_uint32, C.c_uint32]
+            lib.oracle_create_width.restype = C.c_void_p
+            lib.oracle_create_width.argtypes = [C.c_uint32, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32]
             lib.oracle_destroy.argtypes = [C.c_void_p]
             lib.oracle_hash.restype = C.c_uint32
             lib.oracle_hash.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]
@@ -89,11 +91,16 @@ class OracleTable:
     """A slab hash as its plain definition: B insertion-ordered slot arrays."""
 
     def __init__(self, num_buckets: int, hash_a: int, hash_b: int, key_only: bool = False,
-                 lib=None):
+                 lib=None, slab_bytes: int = 128):
         self.lib = lib if lib is not None else load_oracle()
         self.B = int(num_buckets)
         self.key_only = bool(key_only)
-        self.h = self.lib.oracle_create(self.B, int(self.key_only), int(hash_a), int(hash_b))
+        self.slab_bytes = int(slab_bytes)
+        if self.slab_bytes == 128:
+            self.h = self.lib.oracle_create(self.B, int(self.key_only), int(hash_a), int(hash_b))
+        else:
+            self.h = self.lib.oracle_create_width(self.B, int(self.key_only), int(hash_a), int(hash_b),
+                                                  self.slab_bytes)
         if not self.h:
             raise ValueError("oracle_create rejected its arguments")
         self.lines = 0

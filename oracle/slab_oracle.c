@@ -22,9 +22,12 @@
  *     (replace = insert with uniqueness; delete and search act on the only
  *     live instance of k, since keys are unique).
  *   - Slab bookkeeping that follows from the slab layout of Sec. 4.2: M data
- *     elements per slab (M = 15 pairs or 30 keys), so a bucket with `len` used
- *     slots occupies max(1, ceil(len / M)) slabs, and the slot at position s
- *     lies in slab floor(s / M).
+ *     elements per slab, so a bucket with `len` used slots occupies
+ *     max(1, ceil(len / M)) slabs, and the slot at position s lies in slab
+ *     floor(s / M). A slab of W 4-byte words keeps its last two words for the
+ *     auxiliary word and the next pointer, so M = (W - 2) / 2 pairs or W - 2
+ *     keys: 15 or 30 for the paper's 128-byte slab (W = 32), 7 or 14 for a
+ *     64-byte slab (W = 16).
  *   - "Lines touched" per operation: how many slabs a lookup must read in
  *     list order before it stops (Sec. 3.2 search / replace / delete walks).
  *
@@ -58,7 +61,7 @@ typedef struct {
     uint32_t B;        /* number of buckets (base slabs) */
     int learned;       /* buckets from the learned model instead of the universal hash */
     float model[2 + 2 * 1024];
-    uint32_t M;        /* data elements per slab: 15 (key-value) or 30 (key only) */
+    uint32_t M;        /* data elements per slab: 15 / 30 (128-byte slabs) or 7 / 14 (64-byte) */
     int key_only;
     int multiset;      /* duplicates allowed: INSERT instead of REPLACE, deletes empty their slot */
     uint64_t a, b, p;  /* universal hash parameters */
@@ -67,22 +70,30 @@ typedef struct {
     uint64_t reserved; /* ops skipped because their key was a sentinel */
 } or_table;
 
-/* Sec. 3.3: M = 15 pairs per 128-byte slab in key-value mode, 30 keys in key-only
- * mode (Sec. 4.2: lanes 0-29 hold data; lane 30 auxiliary; lane 31 next pointer). */
-or_table *oracle_create(uint32_t num_buckets, int key_only, uint32_t a, uint32_t b)
+/* Sec. 4.2: a slab of W words holds data in words 0..W-3, the auxiliary word in
+ * W-2 and the next pointer in W-1, so M = (W - 2) / 2 pairs in key-value mode and
+ * W - 2 keys in key-only mode. slab_bytes = 4 W is 128 (the paper's slab: M = 15
+ * or 30) or 64 (M = 7 or 14). */
+or_table *oracle_create_width(uint32_t num_buckets, int key_only, uint32_t a, uint32_t b, uint32_t slab_bytes)
 {
-    if (num_buckets == 0) return NULL;
+    if (num_buckets == 0 || (slab_bytes != 64u && slab_bytes != 128u)) return NULL;
     or_table *t = (or_table *)calloc(1, sizeof(or_table));
     if (!t) return NULL;
+    const uint32_t W = slab_bytes / 4u;
     t->B = num_buckets;
     t->key_only = key_only ? 1 : 0;
-    t->M = key_only ? 30u : 15u;
+    t->M = key_only ? W - 2u : (W - 2u) / 2u;
     t->a = a;
     t->b = b;
     t->p = OR_PRIME;
     t->bk = (or_bucket *)calloc(num_buckets, sizeof(or_bucket));
     if (!t->bk) { free(t); return NULL; }
     return t;
+}
+
+or_table *oracle_create(uint32_t num_buckets, int key_only, uint32_t a, uint32_t b)
+{
+    return oracle_create_width(num_buckets, key_only, a, b, 128u);
 }
 
 void oracle_destroy(or_table *t)
@@ -472,8 +483,8 @@ void oracle_stats(const or_table *t, uint32_t *slots, uint32_t *slabs, uint64_t 
 }
 
 /* Sec. 3.3 memory utilization: (x / (M x + y)) * n / sum_i k_i, with x the bytes
- * of one element (8 for a pair, 4 for a key), y = 8 bytes of lanes 30-31, and
- * k_i the number of slabs of bucket i. */
+ * of one element (8 for a pair, 4 for a key), y = 8 bytes of the auxiliary word
+ * and the next pointer, and k_i the number of slabs of bucket i. */
 double oracle_utilization(const or_table *t)
 {
     uint64_t tot[4];

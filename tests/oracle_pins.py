@@ -94,6 +94,22 @@ def pin_slab_boundaries(lib):
         assert int(slabs[0]) == int(want_slabs), (n, slabs[0])
 
 
+def pin_slab_boundaries_64(lib):
+    """A 64-byte slab keeps 7 pairs or 14 keys (Sec. 4.2's layout at 16 words):
+    slot s lies in slab floor(s / M) (tests/golden/slab_boundaries_64.txt)."""
+    for mode, n, key, want_lines, want_slabs in _rows("slab_boundaries_64.txt"):
+        n, key = int(n), int(key)
+        t = OracleTable(1, 1, 0, key_only=mode == "ko", lib=lib, slab_bytes=64)
+        keys = np.arange(100, 100 + n, dtype=np.uint32)
+        t.insert(keys, keys)
+        q = np.array([key if key >= 0 else 99], np.uint32)
+        before = t.lines
+        t.search(q)
+        assert t.lines - before == int(want_lines), (mode, n, key, t.lines - before)
+        _, slabs, _ = t.stats()
+        assert int(slabs[0]) == int(want_slabs), (mode, n, slabs[0])
+
+
 class FlatSet:
     """The Sec. 3.2 definitions written over a plain list of pairs, with no buckets."""
 
@@ -225,50 +241,58 @@ def pin_reserved_keys(lib):
 # ------------------------------------------------------------- slab bookkeeping
 def pin_slab_count_closed_form(lib):
     """A bucket with s used slots has max(1, ceil(s / M)) slabs (M = 15 pairs or
-    30 keys, Sec. 4.2); the lines of n sequential new inserts into one bucket sum
-    to sum_{i<n} (floor(i / M) + 1)."""
-    for key_only, M in ((False, 15), (True, 30)):
-        for n in (0, 1, 14, 15, 16, 29, 30, 31, 44, 45, 46, 100, 451):
-            t = OracleTable(1, 1, 0, key_only=key_only, lib=lib)
+    30 keys per 128-byte slab, 7 or 14 per 64-byte slab, Sec. 4.2); the lines of n
+    sequential new inserts into one bucket sum to sum_{i<n} (floor(i / M) + 1)."""
+    for key_only, M, width in ((False, 15, 128), (True, 30, 128), (False, 7, 64), (True, 14, 64)):
+        for n in (0, 1, 6, 7, 8, 13, 14, 15, 16, 29, 30, 31, 44, 45, 46, 100, 451):
+            t = OracleTable(1, 1, 0, key_only=key_only, lib=lib, slab_bytes=width)
             keys = np.arange(1, n + 1, dtype=np.uint32)
             t.insert(keys, keys)
             slots, slabs, _ = t.stats()
             assert int(slots[0]) == n
-            assert int(slabs[0]) == max(1, -(-n // M)), (key_only, n, slabs[0])
-            assert t.lines == sum(i // M + 1 for i in range(n)), (key_only, n, t.lines)
+            assert int(slabs[0]) == max(1, -(-n // M)), (key_only, width, n, slabs[0])
+            assert t.lines == sum(i // M + 1 for i in range(n)), (key_only, width, n, t.lines)
 
 
 def pin_max_utilization(lib):
     """Sec. 4.2 / Sec. 6.1: a single full bucket reaches the maximum utilization
-    M x / (M x + y) = 120 / 128 (the paper's "94%"), in both modes."""
+    M x / (M x + y) = 120 / 128 (the paper's "94%"), in both modes; a 64-byte slab
+    keeps the same 8 bytes of auxiliary word and next pointer, so 56 / 64."""
     for key_only, M in ((False, 15), (True, 30)):
         t = OracleTable(1, 1, 0, key_only=key_only, lib=lib)
         keys = np.arange(1, 15 * M + 1, dtype=np.uint32)
         t.insert(keys, keys)
         assert abs(t.utilization() - 120.0 / 128.0) < 1e-12, t.utilization()
         assert round(100 * t.utilization()) == 94
+    for key_only, M in ((False, 7), (True, 14)):
+        t = OracleTable(1, 1, 0, key_only=key_only, lib=lib, slab_bytes=64)
+        keys = np.arange(1, 9 * M + 1, dtype=np.uint32)
+        t.insert(keys, keys)
+        assert abs(t.utilization() - 56.0 / 64.0) < 1e-12, t.utilization()
 
 
 def pin_mean_slabs_binomial(lib):
     """Sec. 3.3: keys spread uniformly, so a bucket's load is Binomial(n, 1/B) and
-    its expected slab count is E[max(1, ceil(X / 15))]. At n = 2^16 the oracle's
+    its expected slab count is E[max(1, ceil(X / M))]. At n = 2^16 the oracle's
     mean slabs per bucket must match that expectation within 2 %, for every
-    beta the bulk benchmark sweeps (B = ceil(n / (15 beta)))."""
+    beta the bulk benchmark sweeps (B = ceil(n / (M beta))), with M = 15 pairs per
+    128-byte slab and 7 per 64-byte slab."""
     from scipy.stats import binom
     rng = np.random.default_rng(5)
     n = 1 << 16
     keys = np.unique(rng.integers(0, 0xFFFFFFFE, size=n, dtype=np.uint64)).astype(np.uint32)
     n = len(keys)
-    for beta in (0.2, 0.6, 1.0, 2.0):
-        B = int(np.ceil(n / (15 * beta)))
-        t = OracleTable(B, int(rng.integers(1, P)), int(rng.integers(0, P)), lib=lib)
-        t.insert(keys, keys)
-        _, slabs, tot = t.stats()
-        x = np.arange(0, 15 * 40)
-        pmf = binom.pmf(x, n, 1.0 / B)
-        expect = float((pmf * np.maximum(1, -(-x // 15))).sum())
-        got = tot["slabs"] / B
-        assert abs(got - expect) / expect < 0.02, (beta, got, expect)
+    for M, width in ((15, 128), (7, 64)):
+        for beta in (0.2, 0.6, 1.0, 2.0):
+            B = int(np.ceil(n / (M * beta)))
+            t = OracleTable(B, int(rng.integers(1, P)), int(rng.integers(0, P)), lib=lib, slab_bytes=width)
+            t.insert(keys, keys)
+            _, slabs, tot = t.stats()
+            x = np.arange(0, M * 40)
+            pmf = binom.pmf(x, n, 1.0 / B)
+            expect = float((pmf * np.maximum(1, -(-x // M))).sum())
+            got = tot["slabs"] / B
+            assert abs(got - expect) / expect < 0.02, (width, beta, got, expect)
 
 
 # ------------------------------------------------------------------- SlabAlloc

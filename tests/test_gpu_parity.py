@@ -248,7 +248,7 @@ def test_iteration_cap_counts_slab_reads_across_the_ring(variant, key_only):
 
 
 @pytest.mark.parametrize("variant,tpb,bps", [("staged", 32, 1), ("staged", 128, 2), ("staged", 256, 0),
-                                             ("staged", 512, 1), ("staged", 768, 1), ("direct", 32, 1),
+                                             ("staged", 512, 1), ("staged", 576, 1), ("direct", 32, 1),
                                              ("direct", 128, 2), ("direct", 512, 0), ("direct", 1024, 1)])
 def test_launch_shapes(variant, tpb, bps):
     w = W.bulk_workload(20000, 0.8, 20000, 0.5, 5000, seed=4)

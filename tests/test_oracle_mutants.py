@@ -37,7 +37,9 @@ MUTANTS = {
     "flush_reverses_order": ("if (bk->s[s].live == OR_LIVE) bk->s[w++] = bk->s[s];",
                              "if (bk->s[s].live == OR_LIVE) { or_slot x = bk->s[s]; for (uint32_t q = w++; q > 0; q--) bk->s[q] = bk->s[q - 1]; bk->s[0] = x; }"),
     "slab_count_off_by_one": ("(len + t->M - 1) / t->M", "len / t->M + 1"),
-    "wrong_pairs_per_slab": ("t->M = key_only ? 30u : 15u;", "t->M = key_only ? 30u : 16u;"),
+    "wrong_pairs_per_slab": ("t->M = key_only ? W - 2u : (W - 2u) / 2u;", "t->M = key_only ? W - 2u : W / 2u;"),
+    "slab_width_ignored": ("const uint32_t W = slab_bytes / 4u;", "const uint32_t W = 32u; (void)slab_bytes;"),
+    "aux_word_holds_a_key": ("t->M = key_only ? W - 2u : (W - 2u) / 2u;", "t->M = key_only ? W - 1u : (W - 2u) / 2u;"),
     "search_lines_off_by_one": (
         "*value = t->key_only ? 0 : bk->s[s].value;\n        if (lines) *lines += (uint64_t)s / t->M + 1;",
         "*value = t->key_only ? 0 : bk->s[s].value;\n        if (lines) *lines += (uint64_t)s / t->M;"),
