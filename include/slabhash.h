@@ -85,7 +85,7 @@ typedef struct slab_config {
 typedef struct slab_info {
     uint32_t num_buckets;        /* B: base slabs */
     int32_t mode;                /* enum slab_mode */
-    uint32_t elements_per_slab;  /* M: 15 or 30 */
+    uint32_t elements_per_slab;  /* M: 15 or 30 (128-byte slabs), 7 or 14 (64-byte slabs) */
     uint32_t hash_a, hash_b;     /* universal hash parameters */
     uint64_t pool_slabs;         /* SlabAlloc memory units (multiple of 1024) */
     uint32_t num_memory_blocks;  /* pool_slabs / 1024 */
@@ -94,7 +94,7 @@ typedef struct slab_info {
     uint32_t sm_count;
     uint64_t device_bytes;       /* bytes the table holds on the device */
     int32_t multiset;            /* 1: duplicates allowed (slab_set_multiset) */
-    int32_t pad;
+    int32_t slab_bytes;          /* 128 or 64 (slab_create_width) */
 } slab_info;
 
 /*
@@ -113,6 +113,25 @@ typedef struct slab_info {
  */
 int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b,
                 uint64_t pool_slabs, slab_table **out);
+
+/*
+ * slab_create with the slab width as a parameter: slab_bytes = 128 (the paper's
+ * slab, as slab_create) or 64. Sec. 4.2 sizes the slab to the warp's access
+ * width (32 lanes x 4 bytes) and keeps its last two words for the auxiliary word
+ * and the next pointer; a 64-byte slab is that layout at 16 words: 7 pairs at
+ * even words 0..12 with their values after them (key-value mode) or 14 keys at
+ * words 0..13 (key-only mode), the auxiliary word at 14 and the next pointer at
+ * 15. The SlabAlloc pool then holds 64-byte memory units (still 1024 per memory
+ * block, same bitmaps and addresses). Every batch call, slab_reset, slab_stats,
+ * slab_export, slab_bucket_of, the SlabAlloc calls, slab_grow_pool,
+ * slab_chain_histogram_noalloc, the learned bucket function, the serving loop
+ * and groups take 64-byte tables; the paper-structured variant
+ * (SLAB_VARIANT_DIRECT), multiset tables, SEARCHALL / DELETEALL and FLUSH
+ * return SLAB_ERR_INVALID_ARG for them. Other errors as slab_create; a slab_bytes other
+ * than 64 or 128 is SLAB_ERR_INVALID_ARG.
+ */
+int slab_create_width(uint32_t num_buckets, int mode, uint32_t slab_bytes, uint32_t hash_a, uint32_t hash_b,
+                      uint64_t pool_slabs, slab_table **out);
 
 /* The universal hash parameters drawn from a seed (Sec. 3.3 "a, b random"):
  * with x1, x2 the first two outputs of SplitMix64 seeded with `seed`,
@@ -385,6 +404,11 @@ int slab_grow_pool(slab_table *t, uint64_t extra_slabs);
 typedef struct slab_group slab_group; /* opaque, library-owned */
 int slab_group_create(uint32_t ntables, const uint32_t *h_num_buckets, const uint32_t *h_hash_a,
                       const uint32_t *h_hash_b, const uint64_t *h_pool_slabs, int mode, slab_group **out);
+/* slab_group_create with every table of the group at slab width slab_bytes (128
+ * or 64; see slab_create_width). */
+int slab_group_create_width(uint32_t ntables, const uint32_t *h_num_buckets, const uint32_t *h_hash_a,
+                            const uint32_t *h_hash_b, const uint64_t *h_pool_slabs, int mode, uint32_t slab_bytes,
+                            slab_group **out);
 /* Frees the arena and every table handle of the group. */
 void slab_group_destroy(slab_group *g);
 /* A handle to table i of the group, valid until the group is destroyed; every
@@ -529,17 +553,19 @@ const char *slab_error_string(int rc);
 int slab_probe_random_lines(const uint32_t *d_buf, uint64_t footprint_lines, uint64_t n_reads,
                             uint32_t seed, int lines_in_flight, int threads_per_block,
                             uint32_t *d_sink, void *stream);
-/* slab_probe_random_lines_v4: the same n_reads random whole-line reads, each line
- * read the way the staged kernels move slabs, as eight 16-byte pieces by 8
- * lanes, so one warp instruction covers four lines. form 0: ld.global.cg.v4
- * into registers, lines_in_flight in {4, 8, 16, 32} lines issued per warp
- * before any is consumed. form 1: cp.async.cg 16-byte copies into a 4 KiB
- * shared-memory stage of 32 lines per warp, lines_in_flight 32 (one stage,
- * issued, waited for, consumed) or 64 (two stages: the next 32 lines are issued
- * before this round is consumed). Same buffer, sink and error rules as above;
- * an unsupported form or count returns SLAB_ERR_INVALID_ARG. */
+/* slab_probe_random_lines_v4: n_reads random whole-line reads, each line read the
+ * way the staged kernels move slabs, as 16-byte pieces, so one warp instruction
+ * covers 128 / line_bytes * 4 lines (line_bytes = 128: four lines of 8 lanes;
+ * 64: eight lines of 4 lanes). d_buf holds footprint_lines lines of line_bytes.
+ * form 0: ld.global.cg.v4 into registers, lines_in_flight in {4, 8, 16, 32}
+ * (at least one instruction's worth) lines issued per warp before any is
+ * consumed. form 1: cp.async.cg 16-byte copies into a shared-memory stage of 32
+ * lines per warp, lines_in_flight 32 (one stage, issued, waited for, consumed)
+ * or 64 (two stages: the next 32 lines are issued before this round is
+ * consumed). Same sink and error rules as above; an unsupported form, line size
+ * or count returns SLAB_ERR_INVALID_ARG. */
 int slab_probe_random_lines_v4(const uint32_t *d_buf, uint64_t footprint_lines, uint64_t n_reads,
-                               uint32_t seed, int form, int lines_in_flight, int threads_per_block,
+                               uint32_t seed, int form, int line_bytes, int lines_in_flight, int threads_per_block,
                                uint32_t *d_sink, void *stream);
 int slab_probe_random_cas(unsigned long long *d_buf, uint64_t footprint_lines, uint64_t n_ops,
                           uint32_t seed, int ops_in_flight, int threads_per_block, void *stream);

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/slabhash.h"
@@ -31,6 +32,7 @@ struct slab_group {
     int max_smem_optin = 0;
     uint32_t ntables = 0;
     int mode = 0;
+    uint32_t slab_words = 32;         // words per slab of every table: 32 (128 bytes) or 16 (64 bytes)
     char* d_arena = nullptr;
     uint64_t arena_bytes = 0;
     TableView* d_views = nullptr;     // ntables views (epoch set per launch)
@@ -44,7 +46,8 @@ struct slab_group {
 
 namespace {
 
-constexpr uint32_t kGroupWordsPerWarp = kServeWordsPerWarp;  // stage, ballots, keys, alternate keys
+template <uint32_t kW>
+constexpr uint32_t kGroupWordsPerWarp = kServeWordsPerWarp<kW>;  // stage, ballots, keys, alternate keys
 
 // Tiles of table i: ceil(ops / 32); a decreasing pair of starts counts as no ops.
 __device__ __forceinline__ uint32_t tiles_of(const uint32_t* op_start, uint32_t i) {
@@ -82,58 +85,96 @@ __global__ void tile_prefix_kernel(const uint32_t* op_start, uint32_t ntables, u
 #define SLAB_GROUP_MAXNREG 72
 #endif
 
-template <int kKind, bool kKeyOnly>
+// The group's tiles in order: tile g belongs to the last table whose first tile
+// is <= g (a binary search of the tile prefix), lane op idx of that table's ops.
+// Tables of a group use the universal hash (no learned model), so a tile's
+// buckets need only its table's hash parameters.
+template <int kKind, bool kKeyOnly, uint32_t kW>
 __global__ void __maxnreg__(SLAB_GROUP_MAXNREG)
     group_kernel(const TableView* __restrict__ views, const uint32_t* __restrict__ op_start,
                  const uint32_t* __restrict__ tile_start, uint32_t ntables, uint32_t epoch, BatchArgs A) {
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
     const uint32_t lane = lane_id();
-    uint32_t* buf = smem + (threadIdx.x >> 5) * kGroupWordsPerWarp;
-    uint32_t* ballots = buf + kTileWords;
+    uint32_t* buf = smem + (threadIdx.x >> 5) * kGroupWordsPerWarp<kW>;
+    uint32_t* ballots = buf + kTileWords<kW>;
     uint32_t* skeys = ballots + 32;
     uint32_t* salts = skeys + 32;
     const uint32_t buf_s = (uint32_t)__cvta_generic_to_shared(buf);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t total = tile_start[ntables];
+    uint32_t g = warp_gid;
+    if (g >= total) return;  // warp-uniform
     uint32_t off[8];
-#pragma unroll
-    for (uint32_t j = 0; j < 8; ++j) off[j] = (((lane >> 2) ^ j) << 2) | (lane & 3u);
+    stage_offsets<kW>(lane, off);
     AllocCtx ac{kNoBlock, 0u, 0u};
     uint32_t cur_table = 0xFFFFFFFFu;
 
-    for (uint32_t g = warp_gid; g < total; g += nwarps) {
-        uint32_t lo = 0, hi = ntables;  // the last table whose first tile is <= g
+    // one tile's table, op index and operands (nothing past the group's tiles)
+    struct Tile {
+        uint32_t lo, idx, k, v, o;
+        bool has;
+    };
+    auto fetch = [&](uint32_t gg) {
+        Tile f{0u, 0u, 0u, 0u, kNoOpCode, false};
+        if (gg >= total) return f;
+        uint32_t lo = 0, hi = ntables;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (tile_start[mid] <= g) lo = mid;
+            if (tile_start[mid] <= gg) lo = mid;
             else hi = mid;
         }
-        TableView T = views[lo];
+        f.lo = lo;
+        f.idx = op_start[lo] + (gg - tile_start[lo]) * 32u + lane;
+        f.has = f.idx < op_start[lo + 1] && f.idx < A.n;  // never past the batch arrays
+        if (f.has) {
+            f.o = kKind == kKindMixed ? ld_stream_u8(A.ops + f.idx) : fixed_op<kKind>();
+            f.k = ld_stream(A.keys + f.idx);
+            if (kNeedsValue && A.values) f.v = ld_stream(A.values + f.idx);
+        }
+        return f;
+    };
+    auto walks = [](const Tile& f) { return f.o <= kOpSearch && f.k < kTombstone; };
+    auto bucket = [&](const Tile& f) {
+        if (!walks(f)) return 0u;
+        TableView H{};  // the hash parameters of the tile's table
+        H.hash_a = views[f.lo].hash_a;
+        H.hash_b = views[f.lo].hash_b;
+        H.fastmod_m = views[f.lo].fastmod_m;
+        H.num_buckets = views[f.lo].num_buckets;
+        return universal_bucket(H, f.k);
+    };
+
+    // prologue: this tile hashed, the next one loading
+    Tile c = fetch(g);
+    uint32_t cb = bucket(c);
+    Tile n = fetch(g + nwarps);
+    for (; g < total; g += nwarps) {
+        TableView T = views[c.lo];
         T.epoch = epoch;
-        if (lo != cur_table) {  // resident blocks belong to one table's pool
+        if (c.lo != cur_table) {  // resident blocks belong to one table's pool
             ac = AllocCtx{kNoBlock, 0u, 0u};
-            cur_table = lo;
+            cur_table = c.lo;
         }
-        const uint32_t idx = op_start[lo] + (g - tile_start[lo]) * 32u + lane;
-        const bool has = idx < op_start[lo + 1] && idx < A.n;  // never past the batch arrays
-        uint32_t co = kNoOpCode, ck = 0, cv = 0;
-        if (has) {
-            co = kKind == kKindMixed ? ld_stream_u8(A.ops + idx) : fixed_op<kKind>();
-            ck = ld_stream(A.keys + idx);
-            if (kNeedsValue && A.values) cv = ld_stream(A.values + idx);
-        }
-        const bool walk = co <= kOpSearch && ck < kTombstone;
-        const uint32_t cb = walk ? bucket_of(T, ck) : 0u;
-        stage_slabs(T, buf_s, cb, __ballot_sync(kFull, walk), lane);
+        // (1) this tile's base slabs start moving into the stage
+        stage_slabs<kW>(T, buf_s, cb, __ballot_sync(kFull, walks(c)), lane);
         cp_async_commit();
+        // (2) meanwhile: hash the next tile, start loading the one after it,
+        //     publish this tile's keys
+        const uint32_t nb = bucket(n);
+        const Tile m = fetch(g + 2u * nwarps);
+        skeys[lane] = match_key(T, c.k, c.o);
+        if constexpr (kKind == kKindMixed) salts[lane] = alt_key(c.k, c.o);
+        // (3) serve this tile once its slabs have landed
         cp_async_wait<0>();
-        skeys[lane] = match_key(T, ck, co);
-        if constexpr (kKind == kKindMixed) salts[lane] = alt_key(ck, co);
         __syncwarp();
-        serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb, idx,
-                                    has);
+        serve_tile<kKind, kKeyOnly, kW>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, c.k, c.v, c.o,
+                                        cb, c.idx, c.has);
+        // (4) rotate the pipeline
+        c = n;
+        cb = nb;
+        n = m;
         __syncwarp();
     }
 }
@@ -147,7 +188,8 @@ __global__ void group_reset_kernel(const TableView* views, uint32_t ntables) {
         const TableView T = views[i];
         uint4* base = reinterpret_cast<uint4*>(T.slabs);
         uint4* pool = reinterpret_cast<uint4*>(T.pool);
-        const uint64_t base16 = (uint64_t)T.num_buckets * 8;
+        const uint32_t pieces = T.slab_words / 4u;  // 16-byte pieces per slab
+        const uint64_t base16 = (uint64_t)T.num_buckets * pieces;
         for (uint64_t k = threadIdx.x; k < base16; k += blockDim.x) base[k] = ones;
         const uint64_t words = (uint64_t)T.num_blocks * 32;
         for (uint64_t w = threadIdx.x; w < words; w += blockDim.x) {
@@ -156,9 +198,8 @@ __global__ void group_reset_kernel(const TableView* views, uint32_t ntables) {
             T.bitmaps[w] = 0;
             const uint64_t first = (w >> 5) * kUnitsPerBlock + (w & 31u) * 32u;
             for (; bits; bits &= bits - 1u) {
-                uint4* slab = pool + (first + (uint64_t)(__ffs(bits) - 1)) * 8u;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) slab[c] = ones;
+                uint4* slab = pool + (first + (uint64_t)(__ffs(bits) - 1)) * pieces;
+                for (uint32_t c = 0; c < pieces; ++c) slab[c] = ones;
             }
         }
         if (threadIdx.x == 0) T.status[0] = 0;
@@ -177,12 +218,12 @@ __global__ void group_status_kernel(const TableView* views, uint32_t ntables, ui
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
-template <int kKind, bool kKeyOnly>
+template <int kKind, bool kKeyOnly, uint32_t kW>
 int launch_group(slab_group* g, const uint32_t* d_op_start, const BatchArgs& a, void* stream) {
     const int tpb = g->cfg.threads_per_block;
-    const size_t smem = (size_t)(tpb / 32) * kGroupWordsPerWarp * 4;
+    const size_t smem = (size_t)(tpb / 32) * kGroupWordsPerWarp<kW> * 4;
     if ((int)smem > g->max_smem_optin) return SLAB_ERR_INVALID_ARG;
-    auto k = group_kernel<kKind, kKeyOnly>;
+    auto k = group_kernel<kKind, kKeyOnly, kW>;
     if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SLAB_ERR_CUDA;
     int bps = g->cfg.blocks_per_sm;
@@ -201,24 +242,30 @@ int launch_group(slab_group* g, const uint32_t* d_op_start, const BatchArgs& a, 
 template <int kKind>
 int group_dispatch(slab_group* g, const uint32_t* d_op_start, const BatchArgs& a, void* stream) {
     if (a.n == 0) return SLAB_OK;
-    return g->mode == SLAB_MODE_KEY_ONLY ? launch_group<kKind, true>(g, d_op_start, a, stream)
-                                         : launch_group<kKind, false>(g, d_op_start, a, stream);
+    const bool ko = g->mode == SLAB_MODE_KEY_ONLY;
+    if (g->slab_words == 16u)
+        return ko ? launch_group<kKind, true, 16u>(g, d_op_start, a, stream)
+                  : launch_group<kKind, false, 16u>(g, d_op_start, a, stream);
+    return ko ? launch_group<kKind, true, 32u>(g, d_op_start, a, stream)
+              : launch_group<kKind, false, 32u>(g, d_op_start, a, stream);
 }
 
 }  // namespace
 
 extern "C" {
 
-int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uint32_t* h_hash_a,
-                      const uint32_t* h_hash_b, const uint64_t* h_pool_slabs, int mode, slab_group** out) {
+int slab_group_create_width(uint32_t ntables, const uint32_t* h_num_buckets, const uint32_t* h_hash_a,
+                            const uint32_t* h_hash_b, const uint64_t* h_pool_slabs, int mode, uint32_t slab_bytes,
+                            slab_group** out) {
     if (!out) return SLAB_ERR_INVALID_ARG;
     *out = nullptr;
     if (ntables == 0 || ntables > (1u << 20) || !h_num_buckets || !h_hash_a || !h_hash_b || !h_pool_slabs ||
-        (mode != SLAB_MODE_KEY_VALUE && mode != SLAB_MODE_KEY_ONLY))
+        (mode != SLAB_MODE_KEY_VALUE && mode != SLAB_MODE_KEY_ONLY) || (slab_bytes != 64u && slab_bytes != 128u))
         return SLAB_ERR_INVALID_ARG;
     // arena layout: [slabs of every table][bitmaps of every table][128-byte status block per table]
     std::vector<uint64_t> slab_off(ntables), bm_off(ntables), misc_off(ntables), pools(ntables);
-    uint64_t slab_bytes = 0, bm_bytes = 0;
+    const uint64_t slab_bytes_each = slab_bytes;
+    uint64_t all_slab_bytes = 0, bm_bytes = 0;
     for (uint32_t i = 0; i < ntables; ++i) {
         const uint32_t B = h_num_buckets[i];
         if (B == 0 || h_hash_a[i] == 0 || h_hash_a[i] >= kPrime || h_hash_b[i] >= kPrime || h_pool_slabs[i] == 0)
@@ -226,8 +273,8 @@ int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uin
         const uint64_t blocks = (h_pool_slabs[i] + kUnitsPerBlock - 1) / kUnitsPerBlock;
         if (blocks >= (1ull << 22) || (uint64_t)B + blocks * kUnitsPerBlock > 0xFFFFFFFEull) return SLAB_ERR_INVALID_ARG;
         pools[i] = blocks * kUnitsPerBlock;
-        slab_off[i] = slab_bytes;
-        slab_bytes += align256(((uint64_t)B + pools[i]) * 128ull);
+        slab_off[i] = all_slab_bytes;
+        all_slab_bytes += align256(((uint64_t)B + pools[i]) * slab_bytes_each);
         bm_off[i] = bm_bytes;
         bm_bytes += align256(blocks * 128ull);
     }
@@ -236,6 +283,7 @@ int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uin
     if (!g) return SLAB_ERR_CUDA;
     g->ntables = ntables;
     g->mode = mode;
+    g->slab_words = slab_bytes_each / 4u;
     g->cfg.variant = SLAB_VARIANT_STAGED;
     g->cfg.threads_per_block = 128;
     g->cfg.blocks_per_sm = 0;
@@ -252,7 +300,7 @@ int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uin
         }
         int l2 = 0;
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device);
-        g->arena_bytes = slab_bytes + bm_bytes + misc_bytes;
+        g->arena_bytes = all_slab_bytes + bm_bytes + misc_bytes;
         if (cudaMalloc(&g->d_arena, g->arena_bytes) != cudaSuccess ||
             cudaMalloc(&g->d_views, sizeof(TableView) * ntables) != cudaSuccess ||
             cudaMalloc(&g->d_tile_start, 4ull * (ntables + 1)) != cudaSuccess ||
@@ -260,8 +308,8 @@ int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uin
             rc = SLAB_ERR_CUDA;
             break;
         }
-        if (cudaMemset(g->d_arena, 0xFF, slab_bytes) != cudaSuccess ||
-            cudaMemset(g->d_arena + slab_bytes, 0, bm_bytes + misc_bytes) != cudaSuccess) {
+        if (cudaMemset(g->d_arena, 0xFF, all_slab_bytes) != cudaSuccess ||
+            cudaMemset(g->d_arena + all_slab_bytes, 0, bm_bytes + misc_bytes) != cudaSuccess) {
             rc = SLAB_ERR_CUDA;
             break;
         }
@@ -281,16 +329,17 @@ int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uin
             t->l2_bytes = l2;
             t->num_buckets = h_num_buckets[i];
             t->mode = mode;
+            t->slab_words = g->slab_words;
             t->hash_a = h_hash_a[i];
             t->hash_b = h_hash_b[i];
             t->fastmod_m = UINT64_MAX / h_num_buckets[i] + 1;
             t->pool_slabs = pools[i];
             t->num_blocks = (uint32_t)(pools[i] / kUnitsPerBlock);
             t->d_slabs = reinterpret_cast<uint32_t*>(g->d_arena + slab_off[i]);
-            t->d_bitmaps = reinterpret_cast<uint32_t*>(g->d_arena + slab_bytes + bm_off[i]);
-            t->d_misc = reinterpret_cast<uint32_t*>(g->d_arena + slab_bytes + bm_bytes + 128ull * i);
+            t->d_bitmaps = reinterpret_cast<uint32_t*>(g->d_arena + all_slab_bytes + bm_off[i]);
+            t->d_misc = reinterpret_cast<uint32_t*>(g->d_arena + all_slab_bytes + bm_bytes + 128ull * i);
             t->d_model = nullptr;
-            t->device_bytes = ((uint64_t)t->num_buckets + pools[i]) * 128ull + (uint64_t)t->num_blocks * 128 + 128;
+            t->device_bytes = ((uint64_t)t->num_buckets + pools[i]) * slab_bytes_each + (uint64_t)t->num_blocks * 128 + 128;
             t->cfg = g->cfg;
             views[i] = view(t);
         }
@@ -305,6 +354,11 @@ int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uin
     }
     *out = g;
     return SLAB_OK;
+}
+
+int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uint32_t* h_hash_a,
+                      const uint32_t* h_hash_b, const uint64_t* h_pool_slabs, int mode, slab_group** out) {
+    return slab_group_create_width(ntables, h_num_buckets, h_hash_a, h_hash_b, h_pool_slabs, mode, 128u, out);
 }
 
 void slab_group_destroy(slab_group* g) {
@@ -331,23 +385,29 @@ int slab_group_get_config(const slab_group* g, slab_config* out) {
 }
 
 // The largest block every group kernel of a mode can launch (register caps).
-static int group_block_limit(int mode) {
+static int group_block_limit(int mode, uint32_t slab_words) {
     int lim = 1024;
     auto take = [&](const void* k) {
         cudaFuncAttributes a;
         if (cudaFuncGetAttributes(&a, k) == cudaSuccess) lim = std::min(lim, a.maxThreadsPerBlock);
         else cudaGetLastError();
     };
+    auto all = [&](auto ko, auto wd) {
+        constexpr bool K = decltype(ko)::value;
+        constexpr uint32_t W = decltype(wd)::value;
+        take((const void*)group_kernel<kKindSearch, K, W>);
+        take((const void*)group_kernel<kKindInsert, K, W>);
+        take((const void*)group_kernel<kKindDelete, K, W>);
+        take((const void*)group_kernel<kKindMixed, K, W>);
+    };
+    using W16 = std::integral_constant<uint32_t, 16u>;
+    using W32 = std::integral_constant<uint32_t, 32u>;
     if (mode == SLAB_MODE_KEY_ONLY) {
-        take((const void*)group_kernel<kKindSearch, true>);
-        take((const void*)group_kernel<kKindInsert, true>);
-        take((const void*)group_kernel<kKindDelete, true>);
-        take((const void*)group_kernel<kKindMixed, true>);
+        if (slab_words == 16u) all(std::true_type{}, W16{});
+        else all(std::true_type{}, W32{});
     } else {
-        take((const void*)group_kernel<kKindSearch, false>);
-        take((const void*)group_kernel<kKindInsert, false>);
-        take((const void*)group_kernel<kKindDelete, false>);
-        take((const void*)group_kernel<kKindMixed, false>);
+        if (slab_words == 16u) all(std::false_type{}, W16{});
+        else all(std::false_type{}, W32{});
     }
     return lim - lim % 32;
 }
@@ -355,8 +415,8 @@ static int group_block_limit(int mode) {
 int slab_group_set_config(slab_group* g, const slab_config* c) {
     if (!g || !c || c->threads_per_block < 32 || c->threads_per_block > 1024 || c->threads_per_block % 32 ||
         c->blocks_per_sm < 0 || c->blocks_per_sm > 64 || c->iter_limit < 1 || c->random_probes > (1u << 20) ||
-        (uint64_t)(c->threads_per_block / 32) * kGroupWordsPerWarp * 4 > 227 * 1024 ||
-        c->threads_per_block > group_block_limit(g->mode))
+        (uint64_t)(c->threads_per_block / 32) * kGroupWordsPerWarp<32u> * 4 > 227 * 1024 ||
+        c->threads_per_block > group_block_limit(g->mode, g->slab_words))
         return SLAB_ERR_INVALID_ARG;
     if (c->threads_per_block != g->cfg.threads_per_block)
         for (int& o : g->occupancy) o = 0;

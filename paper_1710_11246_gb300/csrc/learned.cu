@@ -213,7 +213,7 @@ int slab_learn_buckets(slab_table* t, const uint32_t* d_keys, uint32_t n, uint32
     int rc = SLAB_OK;
     unsigned long long h_sums[2] = {0, 0};
     uint32_t h_max[2] = {0, 0};
-    const uint32_t per_slab = t->mode == SLAB_MODE_KEY_ONLY ? 30u : 15u;
+    const uint32_t per_slab = t->mode == SLAB_MODE_KEY_ONLY ? t->slab_words - 2u : (t->slab_words - 2u) / 2u;
     do {
         sample_kernel<<<util_grid(t, p, 256), 256, 0, s>>>(d_keys, sample_stride, m, p, sample);
         bitonic_sort_kernel<<<1, 1024, 0, s>>>(sample, p);

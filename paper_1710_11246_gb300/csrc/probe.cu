@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/slabhash.h"
 
@@ -57,38 +58,41 @@ __global__ void probe_lines_kernel(const uint32_t* __restrict__ buf, uint64_t fo
     if (lane == 0) atomicXor(sink, acc);
 }
 
-// The same random lines read the way the staged kernels move slabs: lanes
-// 8g..8g+7 read one line as eight 16-byte pieces, so one warp instruction covers
-// four lines. kCpAsync = false: ld.global.cg.v4 into registers, L lines (L / 4
-// instructions) issued before any is consumed. kCpAsync = true: cp.async.cg
-// 16-byte copies into the warp's shared-memory stage of 32 lines (4 KiB), all
-// 32 lines of a round in flight, then waited for and consumed from the stage;
-// L = 64 double-buffers (two stages, the next round issued before this one is
-// consumed).
-template <bool kCpAsync, int L>
+// The same random lines read the way the staged kernels move slabs: 16 bytes
+// per lane, so a line of kLW words takes kLW / 4 lanes and one warp instruction
+// covers 128 / kLW lines (four 128-byte lines or eight 64-byte ones). kCpAsync =
+// false: ld.global.cg.v4 into registers, L lines issued before any is consumed.
+// kCpAsync = true: cp.async.cg 16-byte copies into the warp's shared-memory stage
+// of 32 lines, all 32 lines of a round in flight, then waited for and consumed
+// from the stage; L = 64 double-buffers (two stages, the next round issued
+// before this one is consumed).
+template <bool kCpAsync, int L, uint32_t kLW>
 __global__ void probe_lines_v4_kernel(const uint32_t* __restrict__ buf, uint64_t footprint, uint64_t n_reads,
                                       uint32_t seed, uint32_t* sink) {
     extern __shared__ __align__(16) uint32_t stage_all[];
+    constexpr uint32_t kLanesPerLine = kLW / 4u, kLinesPerInst = 32u / kLanesPerLine;
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t g = lane >> 3, c = lane & 7u;
+    const uint32_t g = lane / kLanesPerLine, c = lane % kLanesPerLine;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t groups = (n_reads + 31) / 32;
     uint32_t acc = 0;
     if constexpr (!kCpAsync) {
+        constexpr int kInst = L / (int)kLinesPerInst;  // load instructions in flight
+        static_assert(kInst >= 1 && 32 % L == 0, "lines in flight");
         for (uint64_t gr = warp; gr < groups; gr += nwarps) {
             const uint64_t r = gr * 32 + lane;
             const uint32_t my_line = (uint32_t)pick(r, seed, footprint);
             const uint32_t valid = __ballot_sync(0xFFFFFFFFu, r < n_reads);
 #pragma unroll
-            for (int j0 = 0; j0 < 8; j0 += L / 4) {
-                uint4 v[L / 4];
+            for (int j0 = 0; j0 < (int)kLanesPerLine; j0 += kInst) {
+                uint4 v[kInst];
 #pragma unroll
-                for (int j = 0; j < L / 4; ++j) {
-                    const uint32_t s = 4u * (j0 + j) + g;  // the line of group g in instruction j0 + j
+                for (int j = 0; j < kInst; ++j) {
+                    const uint32_t s = kLinesPerInst * (j0 + j) + g;  // the line of group g in instruction j0 + j
                     const uint32_t line = __shfl_sync(0xFFFFFFFFu, my_line, s);
                     if ((valid >> s) & 1u) {
-                        const uint32_t* p = buf + (uint64_t)line * 32 + c * 4u;
+                        const uint32_t* p = buf + (uint64_t)line * kLW + c * 4u;
                         asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
                                      : "=r"(v[j].x), "=r"(v[j].y), "=r"(v[j].z), "=r"(v[j].w)
                                      : "l"(p));
@@ -97,34 +101,35 @@ __global__ void probe_lines_v4_kernel(const uint32_t* __restrict__ buf, uint64_t
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < L / 4; ++j) acc ^= v[j].x ^ v[j].y ^ v[j].z ^ v[j].w;
+                for (int j = 0; j < kInst; ++j) acc ^= v[j].x ^ v[j].y ^ v[j].z ^ v[j].w;
             }
         }
     } else {
         constexpr int kStages = L / 32;
-        uint32_t* stage = stage_all + (threadIdx.x >> 5) * (32u * 32u * kStages);
+        constexpr uint32_t kStageWords = 32u * kLW;
+        uint32_t* stage = stage_all + (threadIdx.x >> 5) * (kStageWords * kStages);
         const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
         auto issue = [&](uint64_t gr, int st) {
             const uint64_t r = gr * 32 + lane;
             const uint32_t my_line = (uint32_t)pick(r, seed, footprint);
             const uint32_t valid = __ballot_sync(0xFFFFFFFFu, gr < groups && r < n_reads);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t s = 4u * j + g;
+            for (uint32_t j = 0; j < kLanesPerLine; ++j) {
+                const uint32_t s = kLinesPerInst * j + g;
                 const uint32_t line = __shfl_sync(0xFFFFFFFFu, my_line, s);
                 if ((valid >> s) & 1u) {
-                    const uint32_t dst = stage_s + (uint32_t)st * 4096u + s * 128u + c * 16u;
+                    const uint32_t dst = stage_s + ((uint32_t)st * kStageWords + s * kLW + c * 4u) * 4u;
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
-                                 "l"(buf + (uint64_t)line * 32 + c * 4u)
+                                 "l"(buf + (uint64_t)line * kLW + c * 4u)
                                  : "memory");
                 }
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
         auto consume = [&](int st) {
-            // each lane xors one word of every staged line of the round
+            // each lane xors one word of every line of the round
 #pragma unroll 8
-            for (int s = 0; s < 32; ++s) acc ^= stage[st * 1024 + s * 32 + lane];
+            for (uint32_t k = lane; k < kStageWords; k += 32u) acc ^= stage[st * kStageWords + k];
         };
         int st = 0;
         if (warp < groups) issue(warp, 0);
@@ -233,47 +238,56 @@ int slab_probe_random_lines(const uint32_t* d_buf, uint64_t footprint_lines, uin
 }
 
 int slab_probe_random_lines_v4(const uint32_t* d_buf, uint64_t footprint_lines, uint64_t n_reads, uint32_t seed,
-                               int form, int lines_in_flight, int threads_per_block, uint32_t* d_sink,
+                               int form, int line_bytes, int lines_in_flight, int threads_per_block, uint32_t* d_sink,
                                void* stream) {
     if (!d_buf || !d_sink || footprint_lines == 0 || footprint_lines >= (1ull << 32) || threads_per_block < 32 ||
-        threads_per_block > 1024 || threads_per_block % 32 || (form != 0 && form != 1))
+        threads_per_block > 1024 || threads_per_block % 32 || (form != 0 && form != 1) ||
+        (line_bytes != 64 && line_bytes != 128))
         return SLAB_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int tpb = threads_per_block;
-    if (form == 0) {
-#define LAUNCH(L)                                                                                         \
-    case L: {                                                                                             \
-        const int g = occupancy_grid((const void*)probe_lines_v4_kernel<false, L>, tpb);                  \
-        probe_lines_v4_kernel<false, L><<<g, tpb, 0, s>>>(d_buf, footprint_lines, n_reads, seed, d_sink); \
-        break;                                                                                            \
-    }
-        switch (lines_in_flight) {
-            LAUNCH(4) LAUNCH(8) LAUNCH(16) LAUNCH(32)
-            default: return SLAB_ERR_INVALID_ARG;
-        }
-#undef LAUNCH
-    } else {
-        const size_t smem = (size_t)(tpb / 32) * 4096u * (size_t)(lines_in_flight / 32);
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (smem > (size_t)optin) return SLAB_ERR_INVALID_ARG;
+    auto run = [&](auto lw) -> int {
+        constexpr uint32_t LW = decltype(lw)::value;
+        if (form == 0) {
 #define LAUNCH(L)                                                                                          \
     case L: {                                                                                              \
-        const void* fn = (const void*)probe_lines_v4_kernel<true, L>;                                      \
+        if constexpr (L >= (int)(128u / LW)) {                                                             \
+            const int g = occupancy_grid((const void*)probe_lines_v4_kernel<false, L, LW>, tpb);           \
+            probe_lines_v4_kernel<false, L, LW><<<g, tpb, 0, s>>>(d_buf, footprint_lines, n_reads, seed, d_sink); \
+            break;                                                                                         \
+        } else {                                                                                           \
+            return SLAB_ERR_INVALID_ARG;                                                                   \
+        }                                                                                                  \
+    }
+            switch (lines_in_flight) {
+                LAUNCH(4) LAUNCH(8) LAUNCH(16) LAUNCH(32)
+                default: return SLAB_ERR_INVALID_ARG;
+            }
+#undef LAUNCH
+        } else {
+            const size_t smem = (size_t)(tpb / 32) * (32u * LW * 4u) * (size_t)(lines_in_flight / 32);
+            int dev = 0, optin = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (smem > (size_t)optin) return SLAB_ERR_INVALID_ARG;
+#define LAUNCH(L)                                                                                          \
+    case L: {                                                                                              \
+        const void* fn = (const void*)probe_lines_v4_kernel<true, L, LW>;                                  \
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) \
             return SLAB_ERR_CUDA;                                                                          \
         const int g = occupancy_grid(fn, tpb, smem);                                                       \
-        probe_lines_v4_kernel<true, L><<<g, tpb, smem, s>>>(d_buf, footprint_lines, n_reads, seed, d_sink); \
+        probe_lines_v4_kernel<true, L, LW><<<g, tpb, smem, s>>>(d_buf, footprint_lines, n_reads, seed, d_sink); \
         break;                                                                                             \
     }
-        switch (lines_in_flight) {
-            LAUNCH(32) LAUNCH(64)
-            default: return SLAB_ERR_INVALID_ARG;
-        }
+            switch (lines_in_flight) {
+                LAUNCH(32) LAUNCH(64)
+                default: return SLAB_ERR_INVALID_ARG;
+            }
 #undef LAUNCH
-    }
-    return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ERR_CUDA;
+        }
+        return cudaGetLastError() == cudaSuccess ? SLAB_OK : SLAB_ERR_CUDA;
+    };
+    return line_bytes == 64 ? run(std::integral_constant<uint32_t, 16u>{}) : run(std::integral_constant<uint32_t, 32u>{});
 }
 
 int slab_probe_random_cas(unsigned long long* d_buf, uint64_t footprint_lines, uint64_t n_ops, uint32_t seed,

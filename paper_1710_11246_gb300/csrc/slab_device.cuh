@@ -20,6 +20,25 @@ constexpr uint32_t kBlocksPerSuper = 1u << 14;
 constexpr uint32_t kKeyLanesKV = 0x15555555u;
 constexpr uint32_t kKeyLanesKeyOnly = 0x3FFFFFFFu;
 
+// Slab geometry for a slab of kW 4-byte words, kW = 32 (the paper's 128-byte
+// slab) or 16 (a 64-byte slab). Sec. 4.2 keeps the last two words for the
+// auxiliary word and the next pointer, so a key-value slab holds (kW - 2) / 2
+// pairs (key at even words 0..kW-4, value after it) and a key-only slab kW - 2
+// keys (words 0..kW-3).
+template <uint32_t kW>
+__host__ __device__ constexpr uint32_t next_word() { return kW - 1u; }
+template <bool kKeyOnly, uint32_t kW>
+__host__ __device__ constexpr uint32_t key_words() {
+    return kKeyOnly ? ((1u << (kW - 2u)) - 1u) : (0x55555555u & ((1u << (kW - 3u)) - 1u));
+}
+template <bool kKeyOnly, uint32_t kW>
+__host__ __device__ constexpr uint32_t elements_per_slab() { return kKeyOnly ? kW - 2u : (kW - 2u) / 2u; }
+template <bool kKeyOnly, uint32_t kW>
+__host__ __device__ constexpr uint32_t last_key_word() { return kKeyOnly ? kW - 3u : kW - 4u; }
+static_assert(key_words<false, 32>() == kKeyLanesKV && key_words<true, 32>() == kKeyLanesKeyOnly,
+              "the 128-byte layout");
+static_assert(key_words<false, 16>() == 0x1555u && key_words<true, 16>() == 0x3FFFu, "the 64-byte layout");
+
 enum : uint32_t { kFlagReserved = 1u, kFlagOutOfSlabs = 2u, kFlagIterLimit = 4u, kFlagBadPointer = 8u };
 enum : uint8_t { kOpInsert = 0, kOpDelete = 1, kOpSearch = 2 };
 // Kernel families by the ops they serve.
@@ -28,7 +47,7 @@ enum : int { kKindSearch = 0, kKindInsert = 1, kKindDelete = 2, kKindMixed = 3 }
 struct TableView {
     uint32_t* slabs;      // B base slabs, then the SlabAlloc pool
     const float* model;   // learned bucket function (root a, b; 1024 leaves a, b)
-    uint32_t* pool;       // slabs + B * 32: unit `a` of the pool at pool + a * 32
+    uint32_t* pool;       // slabs + B * slab_words: unit `a` of the pool at pool + a * slab_words
     uint32_t* bitmaps;    // 32 words per memory block
     uint32_t* status;     // device status word (kFlag*)
     uint64_t fastmod_m;   // ceil(2^64 / B) for the bucket reduction
@@ -42,6 +61,7 @@ struct TableView {
     uint32_t prefetch_l2; // staged kernels pull the next tile's base slabs into L2 (tables much larger than L2)
     uint32_t learned;     // 1: buckets come from the learned model, 0: from the universal hash
     uint32_t multiset;    // 1: duplicates allowed (INSERT, deletes empty their slot), 0: set (REPLACE, tombstones)
+    uint32_t slab_words;  // words per slab: 32 (128-byte slabs) or 16 (64-byte slabs)
 };
 
 struct BatchArgs {
@@ -148,8 +168,7 @@ __device__ __forceinline__ uint32_t* slab_ptr(const TableView& T, uint32_t bucke
     // cur == kEmptyKey means "the base slab of `bucket`", otherwise a pool address.
     // SlabAlloc-light decode (Sec. 5): the pool is contiguous and the 32-bit
     // address is the linear unit index (super block * 2^14 + block) * 1024 + unit.
-    return cur == kEmptyKey ? T.slabs + (uint64_t)bucket * kWordsPerSlab
-                            : T.pool + (uint64_t)cur * kWordsPerSlab;
+    return cur == kEmptyKey ? T.slabs + (uint64_t)bucket * T.slab_words : T.pool + (uint64_t)cur * T.slab_words;
 }
 
 // --------------------------------------------------------------------------

@@ -37,16 +37,19 @@
 
 namespace slab {
 
-constexpr uint32_t kTileWords = 32u * kWordsPerSlab;  // one slab per lane: 4 KB
+template <uint32_t kW>
+constexpr uint32_t kTileWords = 32u * kW;  // one slab per lane: 4 KB (128-byte slabs) or 2 KB (64-byte)
 constexpr uint32_t kNoOpCode = 0xFFu;
 // per warp: the stage, then 32 ballot words, the tile's 32 keys and, for mixed
 // batches, 32 alternate keys (below)
-constexpr uint32_t kServeWordsPerWarp = kTileWords + 32u + 32u + 32u;
+template <uint32_t kW>
+constexpr uint32_t kServeWordsPerWarp = kTileWords<kW> + 32u + 32u + 32u;
 // Search and delete kernels add the ring of deferred ops behind that: op index,
 // slab to stage next, key and rounds so far, kDeferSlots of each. The largest
 // per-warp layout of the staged kernels is kStagedWordsPerWarp.
 constexpr uint32_t kDeferSlots = 64u;
-constexpr uint32_t kStagedWordsPerWarp = kServeWordsPerWarp + 4u * kDeferSlots;
+template <uint32_t kW>
+constexpr uint32_t kStagedWordsPerWarp = kServeWordsPerWarp<kW> + 4u * kDeferSlots;
 
 // The second value a mixed op's WCWS step matches besides its key: an empty
 // slot for an insert (it may claim one), its key again for a search or delete.
@@ -68,30 +71,61 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Stage position of word w of the slab in slot s. The 16-byte chunks of a slot
-// are rotated by XOR with (s mod 8): a warp reading word `lane` of one slot hits
-// 32 distinct banks, and 32 lanes each reading one word of their own slot hit at
-// most 4 lanes per bank.
+// are rotated by XOR with a function of s: a warp reading all words of one
+// 128-byte slot, or of two adjacent 64-byte slots, hits 32 distinct banks, and
+// 32 lanes each reading one word of their own slot hit at most 4 lanes per bank.
+// 128-byte slots XOR their 8 chunks with s mod 8; 64-byte slots, two to a bank
+// row, XOR their 4 chunks with (s / 2) mod 4.
+template <uint32_t kW>
 __device__ __forceinline__ uint32_t swz(uint32_t s, uint32_t w) {
-    return s * 32u + ((((w >> 2) ^ (s & 7u)) << 2) | (w & 3u));
+    if constexpr (kW == 32u) return s * 32u + ((((w >> 2) ^ (s & 7u)) << 2) | (w & 3u));
+    else return s * 16u + ((((w >> 2) ^ ((s >> 1) & 3u)) << 2) | (w & 3u));
 }
 
 // Copy, for every lane s in `mask`, the slab with unified index shfl(u, s)
 // (base slab b -> b, pool unit a -> B + a) into slot s of the stage at byte
-// address `stage`: lanes 8g..8g+7 move one slab as eight 16-byte pieces, slots
-// g, g + 4, ..., g + 28 in turn. Slot 4j + g has (4j + g) mod 8 = 4 (j mod 2) + g,
-// so a lane's swizzled destinations take two forms, 512 bytes apart per j.
+// address `stage`, as 16-byte pieces. 128-byte slabs: lanes 8g..8g+7 move one
+// slab, slots g, g + 4, ..., g + 28 in turn; slot 4j + g has (4j + g) mod 8 =
+// 4 (j mod 2) + g, so a lane's swizzled destinations take two forms, 512 bytes
+// apart per j. 64-byte slabs: lanes 4g..4g+3 move one slab, slots g, g + 8, ...,
+// g + 24; slot 8j + g has ((8j + g) / 2) mod 4 = (g / 2) mod 4, one form per lane.
+template <uint32_t kW>
 __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, uint32_t u, uint32_t mask,
                                             uint32_t lane) {
-    const uint32_t g = lane >> 3, c = lane & 7u;
-    const uint32_t* src = T.slabs + c * 4u;  // this lane's 16-byte piece of slab 0
-    const uint32_t dst_even = stage + g * 128u + ((c ^ g) << 4);
-    const uint32_t dst_odd = stage + g * 128u + ((c ^ (g | 4u)) << 4);
-    const uint32_t mg = mask >> g;
+    if constexpr (kW == 32u) {
+        const uint32_t g = lane >> 3, c = lane & 7u;
+        const uint32_t* src = T.slabs + c * 4u;  // this lane's 16-byte piece of slab 0
+        const uint32_t dst_even = stage + g * 128u + ((c ^ g) << 4);
+        const uint32_t dst_odd = stage + g * 128u + ((c ^ (g | 4u)) << 4);
+        const uint32_t mg = mask >> g;
+#pragma unroll
+        for (uint32_t j = 0; j < 8; ++j) {
+            const uint32_t us = __shfl_sync(kFull, u, 4u * j + g);
+            if ((mg >> (4u * j)) & 1u)
+                cp_async_16(((j & 1u) ? dst_odd : dst_even) + j * 512u, src + (uint64_t)us * 32u);
+        }
+    } else {
+        const uint32_t g = lane >> 2, c = lane & 3u;
+        const uint32_t* src = T.slabs + c * 4u;
+        const uint32_t dst = stage + g * 64u + ((c ^ ((g >> 1) & 3u)) << 4);
+        const uint32_t mg = mask >> g;
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t us = __shfl_sync(kFull, u, 8u * j + g);
+            if ((mg >> (8u * j)) & 1u) cp_async_16(dst + j * 512u, src + (uint64_t)us * 16u);
+        }
+    }
+}
+
+// Where lane reads word `lane` (128-byte slabs) of slot s, or word lane mod 16
+// of slot 2i + lane / 16 in step i (64-byte slabs), relative to the slot (pair):
+// off[s mod 8] or off[i mod 4] (see swz).
+template <uint32_t kW>
+__device__ __forceinline__ void stage_offsets(uint32_t lane, uint32_t (&off)[8]) {
 #pragma unroll
     for (uint32_t j = 0; j < 8; ++j) {
-        const uint32_t us = __shfl_sync(kFull, u, 4u * j + g);
-        if ((mg >> (4u * j)) & 1u)
-            cp_async_16(((j & 1u) ? dst_odd : dst_even) + j * 512u, src + (uint64_t)us * kWordsPerSlab);
+        if constexpr (kW == 32u) off[j] = (((lane >> 2) ^ j) << 2) | (lane & 3u);
+        else off[j] = ((lane >> 4) << 4) | ((((lane >> 2) & 3u) ^ (j & 3u)) << 2) | (lane & 3u);
     }
 }
 
@@ -99,11 +133,15 @@ __device__ __forceinline__ void stage_slabs(const TableView& T, uint32_t stage, 
 // (bits of `pend`) in lane order; for each op s it compares word `lane` of the
 // op's staged slab (slot s) with the op's key from the shared copy of the tile's
 // keys (an insert also with EMPTY, a mixed op also with its alternate key) and
-// lane 0 stores the ballot in ballots[s]. Three forms of the same loop: all 32
-// ops queued (`full`: keys read and ballots stored four at a time, no
-// branches), `wide` (unrolled over the 32 slots, one predicate per op) and a loop
-// over the set bits (few ops).
-template <int kKind>
+// lane 0 stores the ballot. With 64-byte slabs a slab is half a warp wide (the
+// slab width the paper ties to the warp's, Sec. 4.2, halved), so one step serves
+// two ops: lanes 0-15 match op 2i and lanes 16-31 op 2i + 1, and the step's
+// ballot (ballots[i]) holds both, op 2i in its low half. 128-byte slabs store op
+// s's ballot in ballots[s]. Three forms of the same loop: all 32 ops queued
+// (`full`: keys read and ballots stored four at a time, no branches), `wide`
+// (unrolled over the steps, one predicate per step) and a loop over the set bits
+// (few ops).
+template <int kKind, uint32_t kW>
 __device__ __forceinline__ void wcws_ballots(const uint32_t* buf, uint32_t* ballots, const uint32_t* skeys,
                                              const uint32_t* salts, const uint32_t (&off)[8], uint32_t pend,
                                              bool full, bool wide) {
@@ -119,33 +157,75 @@ __device__ __forceinline__ void wcws_ballots(const uint32_t* buf, uint32_t* ball
         }
         return __ballot_sync(kFull, pred);
     };
-    auto step = [&](uint32_t s, uint32_t data) {
-        const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? salts[s] : 0u);
-        if (lane == 0) ballots[s] = mm;
-    };
-    if (full) {
+    if constexpr (kW == 32u) {
+        auto step = [&](uint32_t s, uint32_t data) {
+            const uint32_t mm = match(data, skeys[s], kKind == kKindMixed ? salts[s] : 0u);
+            if (lane == 0) ballots[s] = mm;
+        };
+        if (full) {
 #pragma unroll
-        for (uint32_t g = 0; g < 8; ++g) {
-            const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
-            const uint4 a4 = kKind == kKindMixed ? *reinterpret_cast<const uint4*>(salts + 4u * g) : k4;
-            const uint32_t s0 = 4u * g;
-            uint4 b4;
-            b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, a4.x);
-            b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, a4.y);
-            b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, a4.z);
-            b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, a4.w);
-            if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
+            for (uint32_t g = 0; g < 8; ++g) {
+                const uint4 k4 = *reinterpret_cast<const uint4*>(skeys + 4u * g);
+                const uint4 a4 = kKind == kKindMixed ? *reinterpret_cast<const uint4*>(salts + 4u * g) : k4;
+                const uint32_t s0 = 4u * g;
+                uint4 b4;
+                b4.x = match(buf[(s0 + 0u) * 32u + off[(s0 + 0u) & 7u]], k4.x, a4.x);
+                b4.y = match(buf[(s0 + 1u) * 32u + off[(s0 + 1u) & 7u]], k4.y, a4.y);
+                b4.z = match(buf[(s0 + 2u) * 32u + off[(s0 + 2u) & 7u]], k4.z, a4.z);
+                b4.w = match(buf[(s0 + 3u) * 32u + off[(s0 + 3u) & 7u]], k4.w, a4.w);
+                if (lane == 0) *reinterpret_cast<uint4*>(ballots + s0) = b4;
+            }
+        } else if (wide) {
+#pragma unroll
+            for (uint32_t s = 0; s < 32; ++s)
+                if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
+        } else {
+            for (uint32_t q = pend; q; q &= q - 1u) {
+                const uint32_t s = (uint32_t)(__ffs(q) - 1);
+                step(s, buf[swz<32u>(s, lane)]);
+            }
         }
-    } else if (wide) {
-#pragma unroll
-        for (uint32_t s = 0; s < 32; ++s)
-            if ((pend >> s) & 1u) step(s, buf[s * 32u + off[s & 7u]]);
     } else {
-        for (uint32_t q = pend; q; q &= q - 1u) {
-            const uint32_t s = (uint32_t)(__ffs(q) - 1);
-            step(s, buf[swz(s, lane)]);
+        const uint32_t h = lane >> 4;  // which op of the step's pair this lane serves
+        auto step = [&](uint32_t i, uint32_t data) {
+            const uint32_t mm = match(data, skeys[2u * i + h], kKind == kKindMixed ? salts[2u * i + h] : 0u);
+            if (lane == 0) ballots[i] = mm;
+        };
+        if (full) {
+#pragma unroll
+            for (uint32_t g = 0; g < 4; ++g) {  // steps 4g..4g+3: ops 8g..8g+7
+                const uint4 ka = *reinterpret_cast<const uint4*>(skeys + 8u * g);
+                const uint4 kb = *reinterpret_cast<const uint4*>(skeys + 8u * g + 4u);
+                const uint4 aa = kKind == kKindMixed ? *reinterpret_cast<const uint4*>(salts + 8u * g) : ka;
+                const uint4 ab = kKind == kKindMixed ? *reinterpret_cast<const uint4*>(salts + 8u * g + 4u) : kb;
+                const uint32_t i0 = 4u * g;
+                uint4 b4;
+                b4.x = match(buf[(i0 + 0u) * 32u + off[(i0 + 0u) & 3u]], h ? ka.y : ka.x, h ? aa.y : aa.x);
+                b4.y = match(buf[(i0 + 1u) * 32u + off[(i0 + 1u) & 3u]], h ? ka.w : ka.z, h ? aa.w : aa.z);
+                b4.z = match(buf[(i0 + 2u) * 32u + off[(i0 + 2u) & 3u]], h ? kb.y : kb.x, h ? ab.y : ab.x);
+                b4.w = match(buf[(i0 + 3u) * 32u + off[(i0 + 3u) & 3u]], h ? kb.w : kb.z, h ? ab.w : ab.z);
+                if (lane == 0) *reinterpret_cast<uint4*>(ballots + i0) = b4;
+            }
+        } else if (wide) {
+#pragma unroll
+            for (uint32_t i = 0; i < 16; ++i)
+                if ((pend >> (2u * i)) & 3u) step(i, buf[i * 32u + off[i & 3u]]);
+        } else {
+            for (uint32_t q = pend; q;) {
+                const uint32_t i = (uint32_t)(__ffs(q) - 1) >> 1;
+                q &= ~(3u << (2u * i));
+                step(i, buf[i * 32u + off[i & 3u]]);
+            }
         }
     }
+}
+
+// The source lane's share of the ballots: op `lane`'s ballot over the words of
+// its slab, restricted to the key words (Sec. 4.2).
+template <bool kKeyOnly, uint32_t kW>
+__device__ __forceinline__ uint32_t own_ballot(const uint32_t* ballots, uint32_t lane) {
+    if constexpr (kW == 32u) return ballots[lane] & key_words<kKeyOnly, 32u>();
+    else return (ballots[lane >> 1] >> ((lane & 1u) * 16u)) & key_words<kKeyOnly, 16u>();
 }
 
 // One WCWS round (Fig. "alg:search") of a search or delete batch for the ops of
@@ -154,30 +234,29 @@ __device__ __forceinline__ void wcws_ballots(const uint32_t* buf, uint32_t* ball
 // every source lane acts on its ballot (reads the value, or writes the tombstone). On return
 // an op that is done has its result in res / fnd and pending cleared; one that
 // goes on has u set to its list's next slab.
-template <int kKind, bool kKeyOnly>
+template <int kKind, bool kKeyOnly, uint32_t kW>
 __device__ __forceinline__ void read_round(const TableView& T, const uint32_t* buf, uint32_t* ballots,
                                            const uint32_t* skeys, const uint32_t (&off)[8], uint32_t pend,
                                            bool& pending, uint32_t& u, uint32_t& res, uint32_t& fnd) {
     static_assert(kKind == kKindSearch || kKind == kKindDelete, "claims serve whole tiles (serve_tile)");
-    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
     const uint32_t lane = lane_id();
-    wcws_ballots<kKind>(buf, ballots, skeys, skeys, off, pend, pend == kFull, __popc(pend) > 8);
+    wcws_ballots<kKind, kW>(buf, ballots, skeys, skeys, off, pend, pend == kFull, __popc(pend) > 8);
     __syncwarp();
     // the source lanes act on their ballots (Sec. 4.3)
-    const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
+    const uint32_t m = pending ? own_ballot<kKeyOnly, kW>(ballots, lane) : 0u;
     if (pending) {
         if (m) {
             const uint32_t d = (uint32_t)(__ffs(m) - 1);
             if constexpr (kKind == kKindSearch) {
-                res = kKeyOnly ? 0u : buf[swz(lane, d + 1u)];
+                res = kKeyOnly ? 0u : buf[swz<kW>(lane, d + 1u)];
             } else {
-                remove_at<kKeyOnly>(T, T.slabs + (uint64_t)u * kWordsPerSlab, d);
+                remove_at<kKeyOnly>(T, T.slabs + (uint64_t)u * kW, d);
                 res = 1u;
             }
             fnd = 1u;
             pending = false;
         } else {
-            const uint32_t nx = buf[swz(lane, kAddressLane)];
+            const uint32_t nx = buf[swz<kW>(lane, next_word<kW>())];
             if (nx == kEmptyKey) {
                 pending = false;  // end of the list: not found
             } else if (valid_next(T, nx)) {
@@ -195,13 +274,12 @@ __device__ __forceinline__ void read_round(const TableView& T, const uint32_t* b
 // buf_s), keys in `skeys` and (mixed) alternate keys in `salts`: the WCWS rounds of Fig.
 // "alg:search", each op's source-lane action, restaging for ops that move on,
 // list growth, and the result writes.
-template <int kKind, bool kKeyOnly>
+template <int kKind, bool kKeyOnly, uint32_t kW>
 __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& A, AllocCtx& ac, uint32_t warp_gid,
                                            const uint32_t* buf, uint32_t buf_s, uint32_t* ballots,
                                            const uint32_t* skeys, const uint32_t* salts, const uint32_t (&off)[8],
                                            uint32_t ck, uint32_t cv, uint32_t co, uint32_t cb, uint32_t idx,
                                            bool has) {
-    constexpr uint32_t kKeyMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
     const uint32_t lane = lane_id();
     bool pending = co <= kOpSearch && ck < kTombstone;
     if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
@@ -213,18 +291,18 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
         if (!pend) break;
         const uint32_t u = cur == kEmptyKey ? cb : T.num_buckets + cur;
         if (!first) {  // restage only the ops that moved on or must retry
-            stage_slabs(T, buf_s, u, pend, lane);
+            stage_slabs<kW>(T, buf_s, u, pend, lane);
             cp_async_commit();
             cp_async_wait<0>();
             __syncwarp();
         }
         // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
-        wcws_ballots<kKind>(buf, ballots, skeys, salts, off, pend, first && pend == kFull, first);
+        wcws_ballots<kKind, kW>(buf, ballots, skeys, salts, off, pend, first && pend == kFull, first);
         __syncwarp();
 
         // the source lanes act on their ballots (Sec. 4.3)
-        const uint32_t m = pending ? (ballots[lane] & kKeyMask) : 0u;
-        uint32_t* gslab = T.slabs + (uint64_t)u * kWordsPerSlab;
+        const uint32_t m = pending ? own_ballot<kKeyOnly, kW>(ballots, lane) : 0u;
+        uint32_t* gslab = T.slabs + (uint64_t)u * kW;
         const uint32_t myop = kKind == kKindMixed ? co : fixed_op<kKind>();
         bool cas_wait = false, cas_new = false, need_slab = false;
         unsigned long long cas_exp = 0, cas_got = 0;
@@ -233,7 +311,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
             if (m) {
                 d = (uint32_t)(__ffs(m) - 1);
                 if (myop == kOpSearch) {
-                    res = kKeyOnly ? 0u : buf[swz(lane, d + 1u)];
+                    res = kKeyOnly ? 0u : buf[swz<kW>(lane, d + 1u)];
                     fnd = 1u;
                     pending = false;
                 } else if (myop == kOpDelete) {
@@ -242,7 +320,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                     fnd = 1u;
                     pending = false;
                 } else if constexpr (kKeyOnly) {
-                    if (!T.multiset && buf[swz(lane, d)] == ck) {  // already present
+                    if (!T.multiset && buf[swz<kW>(lane, d)] == ck) {  // already present
                         res = 0u;
                         fnd = 1u;
                         pending = false;
@@ -253,7 +331,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                         cas_new = true;
                     }
                 } else {
-                    const uint2 pr = *reinterpret_cast<const uint2*>(buf + swz(lane, d));
+                    const uint2 pr = *reinterpret_cast<const uint2*>(buf + swz<kW>(lane, d));
                     cas_exp = pack_pair(pr.x, pr.y);
                     cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
                                         pack_pair(ck, cv));
@@ -261,7 +339,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                     cas_new = pr.x == kEmptyKey;
                 }
             } else {
-                const uint32_t nx = buf[swz(lane, kAddressLane)];
+                const uint32_t nx = buf[swz<kW>(lane, next_word<kW>())];
                 if (nx == kEmptyKey) {
                     if (myop == kOpInsert) need_slab = true;
                     else pending = false;  // end of the list: not found
@@ -280,7 +358,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
         // a successful CAS there keeps keys unique. Claims that meet their own key
         // (a replace race) or run off the slab restage and go round again.
         constexpr uint32_t kPairStride = kKeyOnly ? 1u : 2u;
-        constexpr uint32_t kLastKeyLane = kKeyOnly ? 29u : 28u;
+        constexpr uint32_t kLastKeyLane = last_key_word<kKeyOnly, kW>();
         if constexpr (kKind == kKindInsert || kKind == kKindMixed) {
             while (cas_wait) {
                 if (cas_got == cas_exp) {
@@ -321,7 +399,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
             if (__any_sync(kFull, need_slab)) {
                 const uint32_t peers = __match_any_sync(kFull, need_slab ? (unsigned long long)gslab : 0ull);
                 const int leader = __ffs(peers) - 1;
-                const uint32_t lead_nx = grow_lists(T, ac, warp_gid, gslab, need_slab && (int)lane == leader);
+                const uint32_t lead_nx = grow_lists<kW>(T, ac, warp_gid, gslab, need_slab && (int)lane == leader);
                 const uint32_t nx = __shfl_sync(kFull, lead_nx, leader);
                 if (need_slab) settle(nx);
             }
@@ -330,7 +408,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
             for (uint32_t q = __ballot_sync(kFull, need_slab); q; q &= q - 1u) {
                 const int s = __ffs(q) - 1;
                 uint32_t* ps = reinterpret_cast<uint32_t*>(__shfl_sync(kFull, (unsigned long long)gslab, s));
-                const uint32_t nx = grow_list(T, ac, warp_gid, ps, s);
+                const uint32_t nx = grow_list<kW>(T, ac, warp_gid, ps, s);
                 if ((int)lane == s) settle(nx);
             }
         }
@@ -365,18 +443,20 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
 template <int kKind>
 constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
 // shared memory words per warp of a kind's kernel (the ring only where ops wait in one)
-template <int kKind>
-constexpr uint32_t kWordsPerWarp = kClaims<kKind> ? kServeWordsPerWarp : kStagedWordsPerWarp;
+template <int kKind, uint32_t kW>
+constexpr uint32_t kWordsPerWarp = kClaims<kKind> ? kServeWordsPerWarp<kW> : kStagedWordsPerWarp<kW>;
 
-template <int kKind, bool kKeyOnly>
+// kW: words per slab, 32 (128-byte slabs) or 16 (64-byte slabs)
+template <int kKind, bool kKeyOnly, uint32_t kW>
 __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
                                                 : (kClaims<kKind> ? SLAB_CLAIM_MAXNREG : SLAB_READ_MAXNREG))
     staged_kernel(TableView T, BatchArgs A) {
+    static_assert(kW == 32u || kW == 16u, "128- or 64-byte slabs");
     extern __shared__ __align__(16) uint32_t smem[];
     constexpr bool kNeedsValue = (kKind == kKindInsert || kKind == kKindMixed) && !kKeyOnly;
     const uint32_t lane = lane_id();
-    uint32_t* buf = smem + (threadIdx.x >> 5) * kWordsPerWarp<kKind>;
-    uint32_t* ballots = buf + kTileWords;
+    uint32_t* buf = smem + (threadIdx.x >> 5) * kWordsPerWarp<kKind, kW>;
+    uint32_t* ballots = buf + kTileWords<kW>;
     uint32_t* skeys = ballots + 32;
     uint32_t* salts = skeys + 32;
     uint32_t* q_idx = salts + 32;  // the ring (search and delete kernels)
@@ -394,10 +474,8 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
     uint32_t t = warp_gid;
     if (t >= ntiles) return;  // warp-uniform
 
-    // word `lane` of slot s sits at s * 32 + off[s & 7]
     uint32_t off[8];
-#pragma unroll
-    for (uint32_t j = 0; j < 8; ++j) off[j] = (((lane >> 2) ^ j) << 2) | (lane & 3u);
+    stage_offsets<kW>(lane, off);
 
     AllocCtx ac{kNoBlock, 0u, 0u};
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -443,19 +521,19 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
     uint32_t ck, cv, co;
     fetch(t, ck, cv, co);
     uint32_t cb = walks(ck, co) ? bucket_of(T, ck) : 0u;
-    if (T.prefetch_l2 && walks(ck, co)) prefetch_l2(T.slabs + (uint64_t)cb * kWordsPerSlab);
+    if (T.prefetch_l2 && walks(ck, co)) prefetch_l2(T.slabs + (uint64_t)cb * kW);
     uint32_t nk, nv, no;
     fetch(t + nwarps, nk, nv, no);
 
     for (; t < ntiles; t += nwarps) {
         // (1) this tile's base slabs start moving into the stage
-        stage_slabs(T, buf_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
+        stage_slabs<kW>(T, buf_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
         cp_async_commit();
         // (2) meanwhile: hash the next tile (pulling its slabs into L2 for big
         //     tables), start loading the tile after it, publish this tile's keys
         const bool nwalk = walks(nk, no);
         const uint32_t nb = nwalk ? bucket_of(T, nk) : 0u;
-        if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kWordsPerSlab);
+        if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kW);
         uint32_t mk, mv, mo;
         fetch(t + 2u * nwarps, mk, mv, mo);
         skeys[lane] = match_key(T, ck, co);  // the WCWS steps read keys four at a time from here
@@ -465,11 +543,11 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
         __syncwarp();
         const uint32_t idx = t * 32u + lane;
         if constexpr (kClaims<kKind>) {
-            serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb,
-                                        idx, idx < A.n);
+            serve_tile<kKind, kKeyOnly, kW>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co,
+                                            cb, idx, idx < A.n);
         } else if (T.prefetch_l2) {
-            serve_tile<kKind, kKeyOnly>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co, cb,
-                                        idx, idx < A.n);
+            serve_tile<kKind, kKeyOnly, kW>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, ck, cv, co,
+                                            cb, idx, idx < A.n);
         } else {
             // the tile's first round; the ops that go on join the ring
             if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
@@ -477,7 +555,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
             const uint32_t pend = __ballot_sync(kFull, pending);
             uint32_t res = default_result(co), fnd = 0u, u = cb, r = 0u;
             if (pend) {
-                read_round<kKind, kKeyOnly>(T, buf, ballots, skeys, off, pend, pending, u, res, fnd);
+                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pend, pending, u, res, fnd);
                 round_done(pending, r);
             }
             if (idx < A.n && !pending) {
@@ -503,14 +581,14 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
                 qh = (qh + take) & (kDeferSlots - 1u);
                 qn -= take;
                 const uint32_t pm = take >= 32u ? kFull : (1u << take) - 1u;
-                stage_slabs(T, buf_s, uu, pm, lane);
+                stage_slabs<kW>(T, buf_s, uu, pm, lane);
                 cp_async_commit();
                 skeys[lane] = match_key(T, k, fixed_op<kKind>());
                 cp_async_wait<0>();
                 __syncwarp();
                 bool more = mine;
                 uint32_t rs = default_result(fixed_op<kKind>()), fd = 0u;
-                read_round<kKind, kKeyOnly>(T, buf, ballots, skeys, off, pm, more, uu, rs, fd);
+                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pm, more, uu, rs, fd);
                 round_done(more, rr);
                 if (mine && !more) {
                     if (A.results) A.results[i] = rs;

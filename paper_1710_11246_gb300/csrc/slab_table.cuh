@@ -14,6 +14,7 @@ struct slab_table {
     int sm_count = 0;
     uint32_t num_buckets = 0;
     int mode = 0;
+    uint32_t slab_words = 32;         // words per slab: 32 (128-byte slabs) or 16 (64-byte slabs)
     uint32_t hash_a = 0, hash_b = 0;
     uint64_t fastmod_m = 0;
     uint64_t pool_slabs = 0;
@@ -44,7 +45,7 @@ inline unsigned long long* counters(const slab_table* t) {
 inline slab::TableView view(slab_table* t) {
     slab::TableView v;
     v.slabs = t->d_slabs;
-    v.pool = t->d_slabs + (uint64_t)t->num_buckets * slab::kWordsPerSlab;
+    v.pool = t->d_slabs + (uint64_t)t->num_buckets * t->slab_words;
     v.bitmaps = t->d_bitmaps;
     v.status = t->d_misc;
     v.model = t->d_model;
@@ -57,9 +58,10 @@ inline slab::TableView view(slab_table* t) {
     v.iter_limit = t->cfg.iter_limit;
     v.random_probes = t->cfg.random_probes;
     v.epoch = ++t->epoch;
-    v.prefetch_l2 = (uint64_t)t->num_buckets * 128ull > (uint64_t)t->l2_bytes / 2;
+    v.prefetch_l2 = (uint64_t)t->num_buckets * t->slab_words * 4ull > (uint64_t)t->l2_bytes / 2;
     v.learned = t->learned ? 1u : 0u;
     v.multiset = t->multiset ? 1u : 0u;
+    v.slab_words = t->slab_words;
     return v;
 }
 

@@ -75,16 +75,17 @@ __device__ __forceinline__ uint32_t default_result(uint32_t op) {
 // lane's current slab). Returns the slab to continue with, or kAllocFailed.
 // The link is a 32-bit CAS of the empty next pointer (Sec. 4.3.2); a warp that
 // loses the race returns its slab to SlabAlloc and follows the winner's.
+template <uint32_t kW = kWordsPerSlab>
 __device__ __forceinline__ uint32_t grow_list(const TableView& T, AllocCtx& ac, uint32_t warp_gid,
                                               uint32_t* p_src_lane, int s) {
     uint32_t na = warp_allocate(T, ac, warp_gid);
     if (na == kAllocFailed) {  // no slab left: follow a slab another op linked meanwhile, if any
         uint32_t nx = kAllocFailed;
-        if ((int)lane_id() == s) nx = ld_coherent(p_src_lane + kAddressLane);
+        if ((int)lane_id() == s) nx = ld_coherent(p_src_lane + next_word<kW>());
         return __shfl_sync(kFull, nx, s);  // kEmptyKey (= kAllocFailed) while still unlinked
     }
     uint32_t old = 0;
-    if ((int)lane_id() == s) old = atomicCAS(p_src_lane + kAddressLane, kEmptyKey, na);
+    if ((int)lane_id() == s) old = atomicCAS(p_src_lane + next_word<kW>(), kEmptyKey, na);
     old = __shfl_sync(kFull, old, s);
     if (old == kEmptyKey) return na;
     if ((int)lane_id() == s) deallocate(T, na);
@@ -99,15 +100,16 @@ __device__ __forceinline__ uint32_t grow_list(const TableView& T, AllocCtx& ac, 
 // kAllocRetry where the warp's batch got no slab this time (the op stays on its
 // slab and tries again in a later round); kAllocFailed where the pool had no
 // slab left. Either way a slab that another op linked meanwhile is followed.
+template <uint32_t kW = kWordsPerSlab>
 __device__ __forceinline__ uint32_t grow_lists(const TableView& T, AllocCtx& ac, uint32_t warp_gid, uint32_t* p,
                                                bool need) {
     const uint32_t na = warp_allocate_many(T, ac, warp_gid, need, true);
     if (!need) return kAllocFailed;
     if (na >= kAllocRetry) {  // kAllocRetry or kAllocFailed
-        const uint32_t nx = ld_coherent(p + kAddressLane);
+        const uint32_t nx = ld_coherent(p + next_word<kW>());
         return nx != kEmptyKey ? nx : na;
     }
-    const uint32_t old = atomicCAS(p + kAddressLane, kEmptyKey, na);
+    const uint32_t old = atomicCAS(p + next_word<kW>(), kEmptyKey, na);
     if (old == kEmptyKey) return na;
     deallocate(T, na);
     return old;

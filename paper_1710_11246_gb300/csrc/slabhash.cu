@@ -9,6 +9,7 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <type_traits>
 
 #include "../../include/slabhash.h"
 #include "slab_device.cuh"
@@ -29,6 +30,19 @@ using slab_host::S;
 using slab_host::util_grid;
 using slab_host::view;
 
+// Calls f(key_only, words_per_slab) with both as compile-time constants
+// (std::integral_constant) for the table's mode and slab width.
+template <class F>
+int with_layout(int mode, uint32_t slab_words, F&& f) {
+    using KO = std::true_type;
+    using KV = std::false_type;
+    using W16 = std::integral_constant<uint32_t, 16u>;
+    using W32 = std::integral_constant<uint32_t, 32u>;
+    const bool ko = mode == SLAB_MODE_KEY_ONLY;
+    if (slab_words == 16u) return ko ? f(KO{}, W16{}) : f(KV{}, W16{});
+    return ko ? f(KO{}, W32{}) : f(KV{}, W32{});
+}
+
 // Set-up of the no-allocation statistics call on device `dev` (defined with it at
 // the end of this file): resolves its scratch array's device address and loads
 // its kernels. Returns false on a CUDA error.
@@ -40,15 +54,16 @@ bool valid_config(const slab_config& c) {
            c.blocks_per_sm >= 0 && c.blocks_per_sm <= 64 && c.iter_limit >= 1 && c.random_probes <= (1u << 20) &&
            // staged kernels hold one 4 KB stage per warp, plus up to 1.4 KB of keys, ballots and waiting ops
            (c.variant != SLAB_VARIANT_STAGED ||
-            c.threads_per_block / 32 * kStagedWordsPerWarp * 4 <= 227 * 1024);
+            c.threads_per_block / 32 * kStagedWordsPerWarp<32u> * 4 <= 227 * 1024);
 }
 
-// The largest block every staged kernel of a mode can launch: their register
-// caps put it below 1024 threads (65,536 registers per SM). Cached per mode.
-int staged_block_limit(int mode) {
-    static std::atomic<int> cached[2] = {0, 0};
-    const int m = mode == SLAB_MODE_KEY_ONLY ? 1 : 0;
-    int lim = cached[m].load(std::memory_order_relaxed);
+// The largest block every staged kernel of a mode and slab width can launch:
+// their register caps put it below 1024 threads (65,536 registers per SM).
+// Cached per layout.
+int staged_block_limit(int mode, uint32_t slab_words) {
+    static std::atomic<int> cached[2][2] = {{0, 0}, {0, 0}};
+    const int m = mode == SLAB_MODE_KEY_ONLY ? 1 : 0, w = slab_words == 16u ? 1 : 0;
+    int lim = cached[m][w].load(std::memory_order_relaxed);
     if (lim) return lim;
     lim = 1024;
     auto take = [&](const void* k) {
@@ -56,19 +71,17 @@ int staged_block_limit(int mode) {
         if (cudaFuncGetAttributes(&a, k) == cudaSuccess) lim = std::min(lim, a.maxThreadsPerBlock);
         else cudaGetLastError();
     };
-    if (m) {
-        take((const void*)staged_kernel<kKindSearch, true>);
-        take((const void*)staged_kernel<kKindInsert, true>);
-        take((const void*)staged_kernel<kKindDelete, true>);
-        take((const void*)staged_kernel<kKindMixed, true>);
-    } else {
-        take((const void*)staged_kernel<kKindSearch, false>);
-        take((const void*)staged_kernel<kKindInsert, false>);
-        take((const void*)staged_kernel<kKindDelete, false>);
-        take((const void*)staged_kernel<kKindMixed, false>);
-    }
+    with_layout(mode, slab_words, [&](auto ko, auto wd) {
+        constexpr bool K = decltype(ko)::value;
+        constexpr uint32_t W = decltype(wd)::value;
+        take((const void*)staged_kernel<kKindSearch, K, W>);
+        take((const void*)staged_kernel<kKindInsert, K, W>);
+        take((const void*)staged_kernel<kKindDelete, K, W>);
+        take((const void*)staged_kernel<kKindMixed, K, W>);
+        return 0;
+    });
     lim -= lim % 32;
-    cached[m].store(lim, std::memory_order_relaxed);
+    cached[m][w].store(lim, std::memory_order_relaxed);
     return lim;
 }
 
@@ -89,24 +102,24 @@ __global__ void fill_kernel(uint4* slabs, uint64_t n16, uint4* bitmaps, uint64_t
 // create, written only after being allocated and linked, and a slab that lost its
 // link race is freed unwritten.
 __global__ void reset_kernel(uint4* base, uint64_t base16, uint4* pool, uint32_t* bitmaps, uint64_t words,
-                             uint32_t* misc) {
+                             uint32_t pieces, uint32_t* misc) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint4 ones = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
     for (uint64_t i = tid; i < base16; i += stride) base[i] = ones;
-    // A warp per bitmap word: lanes 8g..8g+7 write slab 4j + g of the word's 32
-    // (16 bytes each), so one store instruction refills four slabs.
+    // A warp per bitmap word: the word's 32 slabs are 32 * pieces 16-byte pieces
+    // (pieces = 8 for 128-byte slabs, 4 for 64-byte ones), and store k of the warp
+    // refills pieces 32k..32k+31, so one store instruction refills 32 / pieces slabs.
     const uint32_t lane = threadIdx.x & 31u;
     for (uint64_t w = tid >> 5; w < words; w += stride >> 5) {
         const uint32_t bits = bitmaps[w];  // the same word in every lane
         if (!bits) continue;                // warp-uniform
         __syncwarp();
         if (lane == 0) bitmaps[w] = 0;
-        uint4* first = pool + ((w >> 5) * kUnitsPerBlock + (w & 31u) * 32u) * 8u;
-#pragma unroll
-        for (uint32_t j = 0; j < 8; ++j) {
-            const uint32_t slab = 4u * j + (lane >> 3);
-            if ((bits >> slab) & 1u) first[slab * 8u + (lane & 7u)] = ones;
+        uint4* first = pool + ((w >> 5) * kUnitsPerBlock + (w & 31u) * 32u) * pieces;
+        for (uint32_t k = lane; k < 32u * pieces; k += 32u) {
+            const uint32_t slab = k / pieces;
+            if ((bits >> slab) & 1u) first[k] = ones;
         }
     }
     if (tid == 0) misc[0] = 0;
@@ -114,10 +127,11 @@ __global__ void reset_kernel(uint4* base, uint64_t base16, uint4* pool, uint32_t
 
 // One warp per bucket: walk the list, count used and live key lanes and slabs,
 // and check that used slots form a prefix in (slab, lane) order.
-template <bool kKeyOnly>
+// Slabs of kW words: lane w reads word w (lanes kW and up see EMPTY).
+template <bool kKeyOnly, uint32_t kW>
 __global__ void stats_kernel(TableView T, uint32_t* slots, uint32_t* slabs, unsigned long long* acc) {
-    constexpr uint32_t kMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
-    constexpr uint32_t kPerSlab = kKeyOnly ? 30u : 15u;
+    constexpr uint32_t kMask = key_words<kKeyOnly, kW>();
+    constexpr uint32_t kPerSlab = elements_per_slab<kKeyOnly, kW>();
     const uint32_t lane = lane_id();
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -127,7 +141,7 @@ __global__ void stats_kernel(TableView T, uint32_t* slots, uint32_t* slabs, unsi
         bool prefix_ok = true, prev_full = true;
         // a list can hold at most every pool slab plus its base slab
         for (uint64_t guard = 0; guard <= (uint64_t)T.num_blocks * kUnitsPerBlock; ++guard) {
-            const uint32_t w = ld_coherent(slab_ptr(T, b, cur) + lane);
+            const uint32_t w = lane < kW ? ld_coherent(slab_ptr(T, b, cur) + lane) : kEmptyKey;
             const uint32_t u = __ballot_sync(kFull, w != kEmptyKey) & kMask;
             const uint32_t l = __ballot_sync(kFull, w != kEmptyKey && w != kTombstone) & kMask;
             const uint32_t cnt = __popc(u);
@@ -139,7 +153,7 @@ __global__ void stats_kernel(TableView T, uint32_t* slots, uint32_t* slabs, unsi
             used += cnt;
             live += __popc(l);
             ++n;
-            const uint32_t nx = __shfl_sync(kFull, w, kAddressLane);
+            const uint32_t nx = __shfl_sync(kFull, w, next_word<kW>());
             if (nx == kEmptyKey) break;
             if (!valid_next(T, nx)) {
                 prefix_ok = false;
@@ -171,17 +185,17 @@ __global__ void popcount_kernel(const uint32_t* words, uint64_t n, unsigned long
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(acc + 3, c);
 }
 
-template <bool kKeyOnly>
+template <bool kKeyOnly, uint32_t kW>
 __global__ void export_kernel(TableView T, uint32_t* ob, uint32_t* ok, uint32_t* ov, uint64_t cap,
                               unsigned long long* count) {
-    constexpr uint32_t kMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
+    constexpr uint32_t kMask = key_words<kKeyOnly, kW>();
     const uint32_t lane = lane_id();
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t b = warp_gid; b < T.num_buckets; b += nwarps) {
         uint32_t cur = kEmptyKey;
         for (uint64_t guard = 0; guard <= (uint64_t)T.num_blocks * kUnitsPerBlock; ++guard) {
-            const uint32_t w = ld_coherent(slab_ptr(T, b, cur) + lane);
+            const uint32_t w = lane < kW ? ld_coherent(slab_ptr(T, b, cur) + lane) : kEmptyKey;
             const uint32_t v = __shfl_down_sync(kFull, w, 1);
             const uint32_t l = __ballot_sync(kFull, w != kEmptyKey && w != kTombstone) & kMask;
             unsigned long long base = 0;
@@ -195,7 +209,7 @@ __global__ void export_kernel(TableView T, uint32_t* ob, uint32_t* ok, uint32_t*
                     if (ov) ov[at] = kKeyOnly ? 0u : v;
                 }
             }
-            const uint32_t nx = __shfl_sync(kFull, w, kAddressLane);
+            const uint32_t nx = __shfl_sync(kFull, w, next_word<kW>());
             if (nx == kEmptyKey || !valid_next(T, nx)) break;
             cur = nx;
         }
@@ -249,13 +263,14 @@ __global__ void free_kernel(TableView T, const uint32_t* addrs, uint32_t n) {
 #ifndef SLAB_PDL
 #define SLAB_PDL 1
 #endif
-template <int kKind, bool kKeyOnly>
+template <int kKind, bool kKeyOnly, uint32_t kW>
 int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
     if (a.n == 0) return SLAB_OK;
     const TableView T = view(t);
     const int tpb = t->cfg.threads_per_block;
     const int wpb = tpb / 32;
     if (t->cfg.variant == SLAB_VARIANT_DIRECT) {
+        if constexpr (kW != 32u) return SLAB_ERR_INVALID_ARG;  // refused by slab_set_config already
         auto k = direct_kernel<kKind, kKeyOnly>;
         int bps = t->cfg.blocks_per_sm;
         if (bps == 0) {  // the occupancy query costs microseconds: ask once per configuration
@@ -269,8 +284,8 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
         const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(bps, 1) * t->sm_count));
         k<<<grid, tpb, 0, S(stream)>>>(T, a);
     } else {
-        auto k = staged_kernel<kKind, kKeyOnly>;
-        const size_t smem = (size_t)wpb * kWordsPerWarp<kKind> * 4;
+        auto k = staged_kernel<kKind, kKeyOnly, kW>;
+        const size_t smem = (size_t)wpb * kWordsPerWarp<kKind, kW> * 4;
         if ((int)smem > t->max_smem_optin) return SLAB_ERR_INVALID_ARG;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -305,14 +320,15 @@ int launch_batch(slab_table* t, const BatchArgs& a, void* stream) {
 
 template <int kKind>
 int dispatch(slab_table* t, const BatchArgs& a, void* stream) {
-    return t->mode == SLAB_MODE_KEY_ONLY ? launch_batch<kKind, true>(t, a, stream)
-                                         : launch_batch<kKind, false>(t, a, stream);
+    return with_layout(t->mode, t->slab_words, [&](auto ko, auto wd) {
+        return launch_batch<kKind, decltype(ko)::value, decltype(wd)::value>(t, a, stream);
+    });
 }
 
 
 // Every slab EMPTY, every bitmap word zero: the state of a new table.
 int fill_table(slab_table* t, void* stream) {
-    const uint64_t n16 = ((uint64_t)t->num_buckets + t->pool_slabs) * 8;  // uint4 per 16 bytes
+    const uint64_t n16 = ((uint64_t)t->num_buckets + t->pool_slabs) * (t->slab_words / 4u);  // uint4 per 16 bytes
     const uint64_t b16 = (uint64_t)t->num_blocks * 8;
     fill_kernel<<<util_grid(t, n16, 256), 256, 0, S(stream)>>>(
         reinterpret_cast<uint4*>(t->d_slabs), n16, reinterpret_cast<uint4*>(t->d_bitmaps), b16, t->d_misc);
@@ -338,12 +354,13 @@ const char* slab_error_string(int rc) {
     }
 }
 
-int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b,
-                uint64_t pool_slabs, slab_table** out) {
+int slab_create_width(uint32_t num_buckets, int mode, uint32_t slab_bytes, uint32_t hash_a, uint32_t hash_b,
+                      uint64_t pool_slabs, slab_table** out) {
     if (!out) return SLAB_ERR_INVALID_ARG;
     *out = nullptr;
     if (num_buckets == 0 || (mode != SLAB_MODE_KEY_VALUE && mode != SLAB_MODE_KEY_ONLY) ||
-        hash_a == 0 || hash_a >= kPrime || hash_b >= kPrime || pool_slabs == 0)
+        (slab_bytes != 64u && slab_bytes != 128u) || hash_a == 0 || hash_a >= kPrime || hash_b >= kPrime ||
+        pool_slabs == 0)
         return SLAB_ERR_INVALID_ARG;
     const uint64_t blocks = (pool_slabs + kUnitsPerBlock - 1) / kUnitsPerBlock;
     const uint64_t pool = blocks * kUnitsPerBlock;
@@ -363,14 +380,15 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     }
     t->num_buckets = num_buckets;
     t->mode = mode;
+    t->slab_words = slab_bytes / 4u;
     t->hash_a = hash_a;
     t->hash_b = hash_b;
     t->fastmod_m = UINT64_MAX / num_buckets + 1;  // wraps to 0 for B = 1, which yields 0 as needed
     t->pool_slabs = pool;
     t->num_blocks = (uint32_t)blocks;
-    const uint64_t slab_bytes = ((uint64_t)num_buckets + pool) * 128ull;
+    const uint64_t all_slab_bytes = ((uint64_t)num_buckets + pool) * slab_bytes;
     const uint64_t bitmap_bytes = blocks * 128ull;
-    if (cudaMalloc(&t->d_slabs, slab_bytes) != cudaSuccess) { delete t; cudaGetLastError(); return SLAB_ERR_CUDA; }
+    if (cudaMalloc(&t->d_slabs, all_slab_bytes) != cudaSuccess) { delete t; cudaGetLastError(); return SLAB_ERR_CUDA; }
     const uint64_t model_bytes = (2 + 2 * 1024) * sizeof(float);
     if (cudaMalloc(&t->d_bitmaps, bitmap_bytes) != cudaSuccess ||
         cudaMalloc(&t->d_misc, 128) != cudaSuccess || cudaMalloc(&t->d_model, model_bytes) != cudaSuccess) {
@@ -381,7 +399,7 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
         cudaGetLastError();
         return SLAB_ERR_CUDA;
     }
-    t->device_bytes = slab_bytes + bitmap_bytes + 128 + model_bytes;
+    t->device_bytes = all_slab_bytes + bitmap_bytes + 128 + model_bytes;
     t->cfg.variant = SLAB_VARIANT_STAGED;
     t->cfg.threads_per_block = 128;
     t->cfg.blocks_per_sm = 0;
@@ -395,6 +413,11 @@ int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b
     }
     *out = t;
     return SLAB_OK;
+}
+
+int slab_create(uint32_t num_buckets, int mode, uint32_t hash_a, uint32_t hash_b, uint64_t pool_slabs,
+                slab_table** out) {
+    return slab_create_width(num_buckets, mode, 128u, hash_a, hash_b, pool_slabs, out);
 }
 
 // SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
@@ -434,11 +457,12 @@ void slab_destroy(slab_table* t) {
 int slab_reset(slab_table* t, void* stream) {
     if (!t) return SLAB_ERR_INVALID_ARG;
     t->dirty = false;
-    const uint64_t base16 = (uint64_t)t->num_buckets * 8;
+    const uint32_t pieces = t->slab_words / 4u;  // 16-byte pieces per slab
+    const uint64_t base16 = (uint64_t)t->num_buckets * pieces;
     const uint64_t words = (uint64_t)t->num_blocks * 32;
     reset_kernel<<<util_grid(t, std::max(base16, words), 256), 256, 0, S(stream)>>>(
         reinterpret_cast<uint4*>(t->d_slabs), base16,
-        reinterpret_cast<uint4*>(t->d_slabs + (uint64_t)t->num_buckets * kWordsPerSlab), t->d_bitmaps, words,
+        reinterpret_cast<uint4*>(t->d_slabs + (uint64_t)t->num_buckets * t->slab_words), t->d_bitmaps, words, pieces,
         t->d_misc);
     return launch_rc();
 }
@@ -447,7 +471,7 @@ int slab_get_info(const slab_table* t, slab_info* out) {
     if (!t || !out) return SLAB_ERR_INVALID_ARG;
     out->num_buckets = t->num_buckets;
     out->mode = t->mode;
-    out->elements_per_slab = t->mode == SLAB_MODE_KEY_ONLY ? 30u : 15u;
+    out->elements_per_slab = t->mode == SLAB_MODE_KEY_ONLY ? t->slab_words - 2u : (t->slab_words - 2u) / 2u;
     out->hash_a = t->hash_a;
     out->hash_b = t->hash_b;
     out->pool_slabs = t->pool_slabs;
@@ -457,7 +481,7 @@ int slab_get_info(const slab_table* t, slab_info* out) {
     out->sm_count = (uint32_t)t->sm_count;
     out->device_bytes = t->device_bytes;
     out->multiset = t->multiset ? 1 : 0;
-    out->pad = 0;
+    out->slab_bytes = (int32_t)(t->slab_words * 4u);
     return SLAB_OK;
 }
 
@@ -469,8 +493,10 @@ int slab_get_config(const slab_table* t, slab_config* out) {
 
 int slab_set_config(slab_table* t, const slab_config* cfg) {
     if (!t || !cfg || !valid_config(*cfg)) return SLAB_ERR_INVALID_ARG;
-    if (cfg->variant == SLAB_VARIANT_STAGED && cfg->threads_per_block > staged_block_limit(t->mode))
+    if (cfg->variant == SLAB_VARIANT_STAGED && cfg->threads_per_block > staged_block_limit(t->mode, t->slab_words))
         return SLAB_ERR_INVALID_ARG;
+    // the paper-structured kernels read one word per lane of 128-byte slabs only
+    if (cfg->variant == SLAB_VARIANT_DIRECT && t->slab_words != 32u) return SLAB_ERR_INVALID_ARG;
     if (cfg->threads_per_block != t->cfg.threads_per_block)
         for (auto& v : t->occupancy)
             for (int& o : v) o = 0;
@@ -530,11 +556,11 @@ int slab_stats(slab_table* t, uint32_t* d_slots, uint32_t* d_slabs, uint64_t* h_
     if (cudaMemsetAsync(acc, 0, 8 * sizeof(unsigned long long), S(stream)) != cudaSuccess) return SLAB_ERR_CUDA;
     const TableView T = view(t);
     const uint32_t grid = util_grid(t, (uint64_t)t->num_buckets * 32, 256);
-    if (t->mode == SLAB_MODE_KEY_ONLY)
-        stats_kernel<true><<<grid, 256, 0, S(stream)>>>(T, d_slots, d_slabs, acc);
-    else
-        stats_kernel<false><<<grid, 256, 0, S(stream)>>>(T, d_slots, d_slabs, acc);
-    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    const int krc = with_layout(t->mode, t->slab_words, [&](auto ko, auto wd) {
+        stats_kernel<decltype(ko)::value, decltype(wd)::value><<<grid, 256, 0, S(stream)>>>(T, d_slots, d_slabs, acc);
+        return launch_rc();
+    });
+    if (krc != SLAB_OK) return SLAB_ERR_CUDA;
     const uint64_t words = (uint64_t)t->num_blocks * 32;
     popcount_kernel<<<util_grid(t, words, 256), 256, 0, S(stream)>>>(t->d_bitmaps, words, acc);
     if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
@@ -555,11 +581,12 @@ int slab_export(slab_table* t, uint32_t* d_buckets, uint32_t* d_keys, uint32_t* 
     if (cudaMemsetAsync(acc + 6, 0, sizeof(unsigned long long), S(stream)) != cudaSuccess) return SLAB_ERR_CUDA;
     const TableView T = view(t);
     const uint32_t grid = util_grid(t, (uint64_t)t->num_buckets * 32, 256);
-    if (t->mode == SLAB_MODE_KEY_ONLY)
-        export_kernel<true><<<grid, 256, 0, S(stream)>>>(T, d_buckets, d_keys, d_values, capacity, acc + 6);
-    else
-        export_kernel<false><<<grid, 256, 0, S(stream)>>>(T, d_buckets, d_keys, d_values, capacity, acc + 6);
-    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    const int krc = with_layout(t->mode, t->slab_words, [&](auto ko, auto wd) {
+        export_kernel<decltype(ko)::value, decltype(wd)::value><<<grid, 256, 0, S(stream)>>>(T, d_buckets, d_keys,
+                                                                                           d_values, capacity, acc + 6);
+        return launch_rc();
+    });
+    if (krc != SLAB_OK) return SLAB_ERR_CUDA;
     unsigned long long c = 0;
     if (cudaMemcpyAsync(&c, acc + 6, sizeof(c), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess ||
         cudaStreamSynchronize(S(stream)) != cudaSuccess)
@@ -627,7 +654,7 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocTo
 std::mutex g_noalloc_mutex;
 unsigned long long* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-template <bool kKeyOnly>
+template <bool kKeyOnly, uint32_t kW>
 __global__ void chain_histogram_kernel(TableView T, uint32_t n_bins, unsigned long long* acc);
 
 // Device address of g_noalloc_scratch on `dev`, resolved with that device
@@ -651,11 +678,11 @@ unsigned long long* noalloc_scratch(int dev, bool refresh) {
 
 // stats_kernel's walk, binning each list's slab count (last bin: that many or
 // more) in a block-shared histogram that is added to the scratch at the end.
-template <bool kKeyOnly>
+template <bool kKeyOnly, uint32_t kW>
 __global__ void chain_histogram_kernel(TableView T, uint32_t n_bins, unsigned long long* acc) {
     extern __shared__ unsigned int hist[];
-    constexpr uint32_t kMask = kKeyOnly ? kKeyLanesKeyOnly : kKeyLanesKV;
-    constexpr uint32_t kPerSlab = kKeyOnly ? 30u : 15u;
+    constexpr uint32_t kMask = key_words<kKeyOnly, kW>();
+    constexpr uint32_t kPerSlab = elements_per_slab<kKeyOnly, kW>();
     for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     const uint32_t lane = lane_id();
@@ -666,7 +693,7 @@ __global__ void chain_histogram_kernel(TableView T, uint32_t n_bins, unsigned lo
         uint32_t cur = kEmptyKey, used = 0, live = 0, n = 0;
         bool prefix_ok = true, prev_full = true;
         for (uint64_t guard = 0; guard <= (uint64_t)T.num_blocks * kUnitsPerBlock; ++guard) {
-            const uint32_t w = ld_coherent(slab_ptr(T, b, cur) + lane);
+            const uint32_t w = lane < kW ? ld_coherent(slab_ptr(T, b, cur) + lane) : kEmptyKey;
             const uint32_t u = __ballot_sync(kFull, w != kEmptyKey) & kMask;
             const uint32_t l = __ballot_sync(kFull, w != kEmptyKey && w != kTombstone) & kMask;
             const uint32_t cnt = __popc(u);
@@ -677,7 +704,7 @@ __global__ void chain_histogram_kernel(TableView T, uint32_t n_bins, unsigned lo
             used += cnt;
             live += __popc(l);
             ++n;
-            const uint32_t nx = __shfl_sync(kFull, w, kAddressLane);
+            const uint32_t nx = __shfl_sync(kFull, w, next_word<kW>());
             if (nx == kEmptyKey) break;
             if (!valid_next(T, nx)) {
                 prefix_ok = false;
@@ -704,8 +731,10 @@ bool noalloc_setup(int dev) {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return true;  // such devices are refused by the call itself
     // load the call's kernels now, so that its first launch does not
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, chain_histogram_kernel<false>) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, chain_histogram_kernel<true>) != cudaSuccess ||
+    if (cudaFuncGetAttributes(&fa, chain_histogram_kernel<false, 32u>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, chain_histogram_kernel<true, 32u>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, chain_histogram_kernel<false, 16u>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, chain_histogram_kernel<true, 16u>) != cudaSuccess ||
         cudaFuncGetAttributes(&fa, popcount_kernel) != cudaSuccess)
         return false;
     return noalloc_scratch(dev, true) != nullptr;
@@ -737,11 +766,12 @@ extern "C" int slab_chain_histogram_noalloc(slab_table* t, uint32_t n_bins, uint
     const TableView T = view(t);
     const uint32_t grid = util_grid(t, (uint64_t)t->num_buckets * 32, 256);
     const size_t smem = n_bins * sizeof(unsigned int);
-    if (t->mode == SLAB_MODE_KEY_ONLY)
-        chain_histogram_kernel<true><<<grid, 256, smem, S(stream)>>>(T, n_bins, acc);
-    else
-        chain_histogram_kernel<false><<<grid, 256, smem, S(stream)>>>(T, n_bins, acc);
-    if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;
+    const int krc = with_layout(t->mode, t->slab_words, [&](auto ko, auto wd) {
+        chain_histogram_kernel<decltype(ko)::value, decltype(wd)::value><<<grid, 256, smem, S(stream)>>>(T, n_bins,
+                                                                                                       acc);
+        return launch_rc();
+    });
+    if (krc != SLAB_OK) return SLAB_ERR_CUDA;
     const uint64_t words = (uint64_t)t->num_blocks * 32;
     popcount_kernel<<<util_grid(t, words, 256), 256, 0, S(stream)>>>(t->d_bitmaps, words, acc);
     if (launch_rc() != SLAB_OK) return SLAB_ERR_CUDA;

@@ -189,24 +189,25 @@ int launch_all(slab_table* t, const uint32_t* d_keys, uint32_t n, uint32_t cap, 
 extern "C" {
 
 int slab_set_multiset(slab_table* t, int on) {
-    if (!t || !t->owns_memory || t->dirty) return SLAB_ERR_INVALID_ARG;
+    if (!t || !t->owns_memory || t->dirty || (on && t->slab_words != 32u)) return SLAB_ERR_INVALID_ARG;
     t->multiset = on != 0;
     return SLAB_OK;
 }
 
 int slab_search_all_batch(slab_table* t, const uint32_t* d_keys, uint32_t n, uint32_t max_per_key,
                           uint32_t* d_counts, uint32_t* d_values_out, void* stream) {
-    if (!t || (n && (!d_keys || !d_counts || (max_per_key && !d_values_out)))) return SLAB_ERR_INVALID_ARG;
+    if (!t || t->slab_words != 32u || (n && (!d_keys || !d_counts || (max_per_key && !d_values_out))))
+        return SLAB_ERR_INVALID_ARG;
     return launch_all<false>(t, d_keys, n, max_per_key, d_counts, d_values_out, stream);
 }
 
 int slab_delete_all_batch(slab_table* t, const uint32_t* d_keys, uint32_t* d_counts, uint32_t n, void* stream) {
-    if (!t || (n && !d_keys)) return SLAB_ERR_INVALID_ARG;
+    if (!t || t->slab_words != 32u || (n && !d_keys)) return SLAB_ERR_INVALID_ARG;
     return launch_all<true>(t, d_keys, n, 0, d_counts, nullptr, stream);
 }
 
 int slab_flush(slab_table* t, uint64_t* h_released, void* stream) {
-    if (!t) return SLAB_ERR_INVALID_ARG;
+    if (!t || t->slab_words != 32u) return SLAB_ERR_INVALID_ARG;
     unsigned long long* acc = counters(t) + 7;
     if (cudaMemsetAsync(acc, 0, sizeof(unsigned long long), S(stream)) != cudaSuccess) return SLAB_ERR_CUDA;
     const TableView T = view(t);
@@ -234,8 +235,8 @@ int slab_grow_pool(slab_table* t, uint64_t extra_slabs) {
     const uint64_t blocks = (uint64_t)t->num_blocks + add;
     const uint64_t pool = blocks * kUnitsPerBlock;
     if (blocks >= (1ull << 22) || (uint64_t)t->num_buckets + pool > 0xFFFFFFFEull) return SLAB_ERR_INVALID_ARG;
-    const uint64_t old_slab_bytes = ((uint64_t)t->num_buckets + t->pool_slabs) * 128ull;
-    const uint64_t slab_bytes = ((uint64_t)t->num_buckets + pool) * 128ull;
+    const uint64_t old_slab_bytes = ((uint64_t)t->num_buckets + t->pool_slabs) * t->slab_words * 4ull;
+    const uint64_t slab_bytes = ((uint64_t)t->num_buckets + pool) * t->slab_words * 4ull;
     const uint64_t old_bitmap_bytes = (uint64_t)t->num_blocks * 128ull, bitmap_bytes = blocks * 128ull;
     uint32_t *slabs = nullptr, *bitmaps = nullptr;
     if (cudaDeviceSynchronize() != cudaSuccess) return SLAB_ERR_CUDA;

@@ -38,6 +38,7 @@ EXPORTED = [
     "slab_server_get_stats", "slab_server_run",
     "slab_set_multiset", "slab_search_all_batch", "slab_delete_all_batch", "slab_flush", "slab_grow_pool",
     "slab_hash_params", "slab_create_seeded", "slab_probe_random_or", "slab_probe_random_lines_v4",
+    "slab_create_width", "slab_group_create_width",
 ]
 SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY, SLAB_SERVER_GROW_POOL = 64, 1 << 24, 1, 2
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
@@ -54,7 +55,7 @@ class SlabInfo(C.Structure):
                 ("hash_a", C.c_uint32), ("hash_b", C.c_uint32), ("pool_slabs", C.c_uint64),
                 ("num_memory_blocks", C.c_uint32), ("blocks_per_super", C.c_uint32),
                 ("num_super_blocks", C.c_uint32), ("sm_count", C.c_uint32), ("device_bytes", C.c_uint64),
-                ("multiset", C.c_int32), ("pad", C.c_int32)]
+                ("multiset", C.c_int32), ("slab_bytes", C.c_int32)]
 
 
 class SlabLearnReport(C.Structure):
@@ -114,7 +115,9 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_copy_bitmaps": (i32, [vp, vp, u64, vp]),
             "slab_error_string": (C.c_char_p, [i32]),
             "slab_probe_random_lines": (i32, [vp, u64, u64, u32, i32, i32, vp, vp]),
-            "slab_probe_random_lines_v4": (i32, [vp, u64, u64, u32, i32, i32, i32, vp, vp]),
+            "slab_probe_random_lines_v4": (i32, [vp, u64, u64, u32, i32, i32, i32, i32, vp, vp]),
+            "slab_create_width": (i32, [u32, i32, u32, u32, u32, u64, C.POINTER(vp)]),
+            "slab_group_create_width": (i32, [u32, vp, vp, vp, vp, i32, u32, C.POINTER(vp)]),
             "slab_probe_random_cas": (i32, [vp, u64, u64, u32, i32, i32, vp]),
             "slab_chain_histogram_noalloc": (i32, [vp, u32, C.POINTER(u64), C.POINTER(u64), vp]),
             "slab_learn_buckets": (i32, [vp, vp, u32, u32, i32, C.POINTER(SlabLearnReport), vp]),
@@ -186,6 +189,13 @@ def _check(rc: int, what: str):
 
 
 # ------------------------------------------------------------------ C-name API
+def slab_create_width(num_buckets: int, mode: int, slab_bytes: int, hash_a: int, hash_b: int, pool_slabs: int) -> int:
+    h = C.c_void_p()
+    _check(load_library().slab_create_width(num_buckets, mode, slab_bytes, hash_a, hash_b, pool_slabs, C.byref(h)),
+           "slab_create_width")
+    return h.value
+
+
 def slab_create(num_buckets: int, mode: int, hash_a: int, hash_b: int, pool_slabs: int) -> int:
     h = C.c_void_p()
     _check(load_library().slab_create(num_buckets, mode, hash_a, hash_b, pool_slabs, C.byref(h)),
@@ -308,9 +318,10 @@ def slab_probe_random_lines(buf, footprint_lines: int, n_reads: int, seed: int, 
 
 
 def slab_probe_random_lines_v4(buf, footprint_lines: int, n_reads: int, seed: int, form: int, lines_in_flight: int,
-                               threads_per_block: int, sink, stream=None) -> None:
+                               threads_per_block: int, sink, stream=None, line_bytes: int = 128) -> None:
     _check(load_library().slab_probe_random_lines_v4(
-        _dptr(buf, 4, footprint_lines * 32, "buf"), footprint_lines, n_reads, seed, form, lines_in_flight,
+        _dptr(buf, 4, footprint_lines * line_bytes // 4, "buf"), footprint_lines, n_reads, seed, form, line_bytes,
+        lines_in_flight,
         threads_per_block, _dptr(sink, 4, 1, "sink"), _stream(stream)), "slab_probe_random_lines_v4")
 
 
@@ -354,7 +365,8 @@ def slab_chain_histogram_noalloc(t: int, n_bins: int, stream=None):
                       linked=tot[5])
 
 
-def slab_group_create(num_buckets, hash_a, hash_b, pool_slabs, mode: int = SLAB_MODE_KEY_VALUE) -> int:
+def slab_group_create(num_buckets, hash_a, hash_b, pool_slabs, mode: int = SLAB_MODE_KEY_VALUE,
+                      slab_bytes: int = 128) -> int:
     import numpy as np
     nb = np.ascontiguousarray(num_buckets, np.uint32)
     ha = np.ascontiguousarray(hash_a, np.uint32)
@@ -363,8 +375,13 @@ def slab_group_create(num_buckets, hash_a, hash_b, pool_slabs, mode: int = SLAB_
     if not (len(nb) == len(ha) == len(hb) == len(ps)):
         raise ValueError("per-table arrays differ in length")
     g = C.c_void_p()
-    _check(load_library().slab_group_create(len(nb), nb.ctypes.data, ha.ctypes.data, hb.ctypes.data, ps.ctypes.data,
-                                            mode, C.byref(g)), "slab_group_create")
+    if slab_bytes == 128:
+        _check(load_library().slab_group_create(len(nb), nb.ctypes.data, ha.ctypes.data, hb.ctypes.data,
+                                                ps.ctypes.data, mode, C.byref(g)), "slab_group_create")
+    else:
+        _check(load_library().slab_group_create_width(len(nb), nb.ctypes.data, ha.ctypes.data, hb.ctypes.data,
+                                                      ps.ctypes.data, mode, slab_bytes, C.byref(g)),
+               "slab_group_create_width")
     return g.value
 
 
@@ -602,8 +619,9 @@ class SlabHash:
     """Owns one table; methods take and return torch CUDA tensors (int32 storage of uint32 bits)."""
 
     def __init__(self, num_buckets: int, hash_a: int, hash_b: int, pool_slabs: int,
-                 mode: int = SLAB_MODE_KEY_VALUE):
-        self.handle = slab_create(num_buckets, mode, hash_a, hash_b, pool_slabs)
+                 mode: int = SLAB_MODE_KEY_VALUE, slab_bytes: int = 128):
+        self.handle = (slab_create(num_buckets, mode, hash_a, hash_b, pool_slabs) if slab_bytes == 128 else
+                       slab_create_width(num_buckets, mode, slab_bytes, hash_a, hash_b, pool_slabs))
         self.info = slab_get_info(self.handle)
         self.mode = mode
 

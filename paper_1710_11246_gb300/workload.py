@@ -168,12 +168,12 @@ class BulkWorkload:
 
 
 def bulk_workload(n: int, beta: float, n_search: int, hit_rate: float, n_delete: int,
-                  seed: int = 0, num_buckets: int | None = None) -> BulkWorkload:
+                  seed: int = 0, num_buckets: int | None = None, per_slab: int = 15) -> BulkWorkload:
     stream = KeyStream(seed)
     rng = np.random.default_rng([int(seed), 0xB01C])
     keys = stream.take(n)
     a, b = hash_params(seed)
-    B = num_buckets if num_buckets is not None else buckets_for(n, beta)
+    B = num_buckets if num_buckets is not None else buckets_for(n, beta, per_slab)
     sb = search_batch(stream, keys, n_search, hit_rate, rng)
     dels = keys[rng.choice(n, size=min(n_delete, n), replace=False)] if n_delete else \
         np.empty(0, np.uint32)
@@ -185,9 +185,10 @@ def config1(seed: int = 0) -> BulkWorkload:
     return bulk_workload(1 << 16, 0.6, 1 << 16, 0.5, 1 << 14, seed)
 
 
-def config2(beta: float = 0.6, hit_rate: float = 0.5, seed: int = 0) -> BulkWorkload:
-    """2^22 pairs, 2^22 searches at the given hit rate, 2^20 deletes."""
-    return bulk_workload(1 << 22, beta, 1 << 22, hit_rate, 1 << 20, seed)
+def config2(beta: float = 0.6, hit_rate: float = 0.5, seed: int = 0, per_slab: int = 15) -> BulkWorkload:
+    """2^22 pairs, 2^22 searches at the given hit rate, 2^20 deletes; per_slab = M
+    (15 pairs per 128-byte slab, 7 per 64-byte slab) sets B = ceil(n / (M beta))."""
+    return bulk_workload(1 << 22, beta, 1 << 22, hit_rate, 1 << 20, seed, per_slab=per_slab)
 
 
 def _cluster_draws(rng, centres, sigmas, count):
@@ -246,16 +247,16 @@ class GroupWorkload:
 
 
 def group_workload(ntables: int, lo: int, hi: int, beta: float = 0.6, hit_rate: float = 0.5,
-                   seed: int = 0, sizes=None) -> GroupWorkload:
+                   seed: int = 0, sizes=None, per_slab: int = 15) -> GroupWorkload:
     """`ntables` tables with sizes log-uniform in [lo, hi] (or the given sizes), each
-    with B = ceil(n / (15 beta)) and its own hash parameters; one search batch per
-    table of n queries at the hit rate."""
+    with B = ceil(n / (M beta)) (M = per_slab) and its own hash parameters; one
+    search batch per table of n queries at the hit rate."""
     rng = np.random.default_rng([int(seed), 0x6A0])
     if sizes is None:
         sizes = np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), ntables))).astype(np.int64)
     sizes = np.asarray(sizes, np.int64)
     stream = KeyStream(seed + 0x5000)
-    B = np.array([buckets_for(max(int(n), 1), beta) for n in sizes], np.uint32)
+    B = np.array([buckets_for(max(int(n), 1), beta, per_slab) for n in sizes], np.uint32)
     ha = rng.integers(1, HASH_PRIME, ntables).astype(np.uint32)
     hb = rng.integers(0, HASH_PRIME, ntables).astype(np.uint32)
     keys, qk, qp = [], [], []

@@ -27,13 +27,14 @@ class Pair:
     """A GPU table and its oracle twin, fed the same batches."""
 
     def __init__(self, num_buckets, a, b, pool_slabs=None, variant="staged", key_only=False,
-                 n_hint=0, **cfg):
+                 n_hint=0, slab_bytes=128, **cfg):
         self.B = int(num_buckets)
-        pool = pool_slabs if pool_slabs is not None else max(1024, 2 * n_hint // (30 if key_only else 15) + 2048)
+        per = (slab_bytes // 4 - 2) // (1 if key_only else 2)  # elements per slab
+        pool = pool_slabs if pool_slabs is not None else max(1024, 2 * n_hint // per + 2048)
         mode = sh.SLAB_MODE_KEY_ONLY if key_only else sh.SLAB_MODE_KEY_VALUE
-        self.g = sh.SlabHash(self.B, a, b, pool, mode=mode)
+        self.g = sh.SlabHash(self.B, a, b, pool, mode=mode, slab_bytes=slab_bytes)
         self.g.configure(variant=VARIANTS[variant], **cfg)
-        self.o = OracleTable(self.B, a, b, key_only=key_only)
+        self.o = OracleTable(self.B, a, b, key_only=key_only, slab_bytes=slab_bytes)
         self.key_only = key_only
 
     def close(self):
