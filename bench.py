@@ -57,9 +57,10 @@ def ncu_traffic(phase: str):
     return NCU_TRAFFIC.get(phase) if h.hexdigest()[:16] == NCU_TRAFFIC["sources_sha256"] else None
 
 
-def make_step_inputs(seed: int = 0):
-    """The step's batches (deterministic for a seed)."""
-    w = W.config2(BETA, HIT, seed)
+def make_step_inputs(seed: int = 0, per_slab: int = 15):
+    """The step's batches (deterministic for a seed); per_slab = M sets the bucket
+    count B = ceil(n / (M beta)) (15 pairs per 128-byte slab, 7 per 64-byte slab)."""
+    w = W.config2(BETA, HIT, seed, per_slab=per_slab)
     stream = W.KeyStream(seed)
     stream.take(N_KEYS + (N_SEARCH - int(round(N_SEARCH * HIT))))  # skip keys the bulk workload used
     rng = np.random.default_rng([seed, 0x3333])
@@ -80,11 +81,11 @@ def config_dict(extra=None):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def run_oracle_step(w, mb):
+def run_oracle_step(w, mb, slab_bytes: int = 128):
     """One step on the CPU oracle; returns (seconds, lines touched per phase, slabs
     linked per phase). The seconds cover the four batches only."""
     from oracle import OracleTable
-    o = OracleTable(w.num_buckets, w.hash_a, w.hash_b)
+    o = OracleTable(w.num_buckets, w.hash_a, w.hash_b, slab_bytes=slab_bytes)
     lines, linked, dt = {}, {}, 0.0
     slabs = o.stats()[2]["slabs"]
     batches = (("build", lambda: o.insert(w.keys, w.values)), ("search", lambda: o.search(w.search.keys)),
@@ -427,7 +428,8 @@ def e2e_arm(args, t, w, mb, device, stream):
             "overlap": "copies in, batches and copies out on three streams; two alternating device buffer sets"}
 
 
-def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24):
+def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24, line_bytes: int = 128,
+                      quick: bool = False):
     """Best random 128-byte-line read rate (lines/s) at a footprint, over three access
     forms (32 lanes x 4 B per line; 8 lanes x 16 B into registers; 8 lanes x 16 B
     cp.async into a shared-memory stage, as the staged kernels move slabs), lines in
@@ -435,24 +437,27 @@ def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24):
     import torch
 
     from paper_1710_11246_gb300 import slabhash as sh
-    lines = footprint_bytes // 128
-    buf = torch.zeros(lines * 32, dtype=torch.int32, device=device)
+    lines = footprint_bytes // line_bytes
+    buf = torch.zeros(lines * (line_bytes // 4), dtype=torch.int32, device=device)
     sink = torch.zeros(1, dtype=torch.int32, device=device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    forms = [("32x4B", lif, lambda rep, lif, tpb: sh.slab_probe_random_lines(buf, lines, n_reads, rep + 1, lif, tpb,
-                                                                            sink)) for lif in (4, 8, 16)]
-    forms += [("8x16B_ld", lif, lambda rep, lif, tpb: sh.slab_probe_random_lines_v4(buf, lines, n_reads, rep + 1, 0,
-                                                                                   lif, tpb, sink))
-              for lif in (8, 16, 32)]
-    forms += [("8x16B_cp.async", lif, lambda rep, lif, tpb: sh.slab_probe_random_lines_v4(buf, lines, n_reads,
-                                                                                         rep + 1, 1, lif, tpb, sink))
-              for lif in (32, 64)]
+    lanes = line_bytes // 16  # lanes per line in the 16-byte-per-lane forms
+    forms = []
+    if line_bytes == 128 and not quick:
+        forms += [("32x4B", lif, lambda rep, lif, tpb: sh.slab_probe_random_lines(buf, lines, n_reads, rep + 1, lif,
+                                                                                 tpb, sink)) for lif in (4, 8, 16)]
+    forms += [(f"{lanes}x16B_ld", lif, lambda rep, lif, tpb: sh.slab_probe_random_lines_v4(
+        buf, lines, n_reads, rep + 1, 0, lif, tpb, sink, line_bytes=line_bytes))
+        for lif in ((8, 16) if quick else (8, 16, 32))]
+    forms += [(f"{lanes}x16B_cp.async", lif, lambda rep, lif, tpb: sh.slab_probe_random_lines_v4(
+        buf, lines, n_reads, rep + 1, 1, lif, tpb, sink, line_bytes=line_bytes))
+        for lif in ((64,) if quick else (32, 64))]
     best = (0.0, None)
     per_form = {}
     for name, lif, fn in forms:
         for tpb in (256, 512):
             ts = []
-            for rep in range(4):
+            for rep in range(3 if quick else 4):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
@@ -469,7 +474,7 @@ def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24):
     return best
 
 
-def random_cas_probe(device, footprint_bytes: int, n_ops: int = 1 << 22):
+def random_cas_probe(device, footprint_bytes: int, n_ops: int = 1 << 22, quick: bool = False):
     """Best random 64-bit atomicCAS rate (ops/s) on pair slots of lines at a footprint,
     the buffer zeroed before each timing so most CASes claim an empty slot."""
     import torch
@@ -478,10 +483,10 @@ def random_cas_probe(device, footprint_bytes: int, n_ops: int = 1 << 22):
     lines = footprint_bytes // 128
     buf = torch.zeros(lines * 16, dtype=torch.int64, device=device)
     best = (0.0, None)
-    for oif in (2, 4, 8):
+    for oif in ((8,) if quick else (2, 4, 8)):
         for tpb in (256, 512):
             ts = []
-            for rep in range(4):
+            for rep in range(3 if quick else 4):
                 buf.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
@@ -530,49 +535,7 @@ def sweep(args, device):
 
     # bulk: build, search at 0/50/100 % hit, delete, for every beta
     for beta in (W.CONFIG2_BETAS if want("bulk") else ()):
-        w = W.config2(beta, 0.5, args.seed)
-        stream_k = W.KeyStream(args.seed)
-        stream_k.take(N_KEYS + N_SEARCH)
-        rng = np.random.default_rng([args.seed, 0x5EA])
-        absent = stream_k.take(N_SEARCH)
-        hit100 = w.keys[rng.permutation(N_KEYS)]
-        queries = {0.0: absent, 0.5: w.search.keys, 1.0: hit100}
-        t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 21)
-        h = t.handle
-        kb, vb, kd = dev(w.keys), dev(w.values), dev(w.delete_keys)
-        out = torch.empty(N_SEARCH, dtype=torch.int32, device=device)
-        fnd = torch.empty(N_SEARCH, dtype=torch.uint8, device=device)
-
-        def build():
-            sh.slab_reset(h, stream)
-            sh.slab_insert_batch(h, kb, vb, None, stream=stream)
-        ms_build = best(build)  # includes the reset fill
-        with torch.cuda.stream(stream):
-            sh.slab_reset(h, stream)
-            sh.slab_insert_batch(h, kb, vb, None, stream=stream)
-        torch.cuda.synchronize()
-        tot = t.stats()
-        util = 8.0 * tot["live"] / (128.0 * tot["slabs"])
-        rates = {}
-        for hr, q in queries.items():
-            dq = dev(q)
-            ms = best(lambda: sh.slab_search_batch(h, dq, out, fnd, stream=stream))
-            rates[f"search_{int(hr * 100)}"] = round(N_SEARCH / (ms * 1e3), 1)
-        snap = None
-        ms_del = []
-        for _ in range(reps):
-            with torch.cuda.stream(stream):
-                sh.slab_reset(h, stream)
-                sh.slab_insert_batch(h, kb, vb, None, stream=stream)
-            ms_del.append(_time_ms(lambda: sh.slab_delete_batch(h, kd, None, stream=stream), stream, flush))
-        rc, flags = t.status(stream)
-        line = {"sweep": "bulk", "beta": beta, "num_buckets": w.num_buckets, "unit": "Mops/s",
-                "build_incl_reset": round(N_KEYS / (ms_build * 1e3), 1), **rates,
-                "delete": round(N_DELETE / (min(ms_del) * 1e3), 1), "utilization": round(util, 4),
-                "slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4), "status": rc}
-        print(json.dumps(line), flush=True)
-        t.close()
-        del snap
+        print(json.dumps({"sweep": "bulk", **bulk_point(args, device, stream, flush, beta, reps)[0]}), flush=True)
 
     if want("slaballoc"):
         slaballoc_sweep(device, stream, flush, reps)
@@ -592,38 +555,144 @@ def sweep(args, device):
         return
     # concurrent batches at full size: preload 2^22 (beta = 0.6), 64 batches of 2^20
     for ratios in W.CONFIG3_RATIOS:
-        w = W.config2(BETA, HIT, args.seed)
-        ks = W.KeyStream(args.seed)
-        ks.take(N_KEYS + N_SEARCH)
-        rng = np.random.default_rng([args.seed, 0xC0C0])
-        live = w.keys
-        batches = []
-        for _ in range(64):
-            mb, live = W.mixed_batch(ks, live, N_MIXED, ratios, rng)
-            batches.append((torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)))
-        t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 22)
-        h = t.handle
-        res = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+        print(json.dumps({"sweep": "mixed", **mixed_series(args, device, stream, flush, ratios)[0]}), flush=True)
+
+
+def bulk_point(args, device, stream, flush, beta, reps=5, slab_bytes=128):
+    """The bulk benchmark (Sec. 6.1) at one beta: build 2^22 pairs (incl. the reset),
+    search 2^22 keys at 0 / 50 / 100 % hit, delete 2^20 keys, each timed alone after
+    an L2 flush, best of `reps`. Returns (rates, host inputs for the oracle)."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
+    per = (slab_bytes // 4 - 2) // 2
+    w = W.config2(beta, 0.5, args.seed, per_slab=per)
+    stream_k = W.KeyStream(args.seed)
+    stream_k.take(N_KEYS + N_SEARCH)
+    rng = np.random.default_rng([args.seed, 0x5EA])
+    absent = stream_k.take(N_SEARCH)
+    hit100 = w.keys[rng.permutation(N_KEYS)]
+    queries = {0.0: absent, 0.5: w.search.keys, 1.0: hit100}
+    t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 21, slab_bytes=slab_bytes)
+    h = t.handle
+    kb, vb, kd = dev(w.keys), dev(w.values), dev(w.delete_keys)
+    out = torch.empty(N_SEARCH, dtype=torch.int32, device=device)
+    fnd = torch.empty(N_SEARCH, dtype=torch.uint8, device=device)
+
+    def best(fn):
+        return min(_time_ms(fn, stream, flush) for _ in range(reps))
+
+    def build():
+        sh.slab_reset(h, stream)
+        sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+    ms_build = best(build)  # includes the reset fill
+    with torch.cuda.stream(stream):
+        sh.slab_reset(h, stream)
+        sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+    torch.cuda.synchronize()
+    tot = t.stats()
+    util = 8.0 * tot["live"] / (float(slab_bytes) * tot["slabs"])
+    rates = {}
+    for hr, q in queries.items():
+        dq = dev(q)
+        ms = best(lambda: sh.slab_search_batch(h, dq, out, fnd, stream=stream))
+        rates[f"search_{int(hr * 100)}"] = round(N_SEARCH / (ms * 1e3), 1)
+    ms_del = []
+    for _ in range(reps):
         with torch.cuda.stream(stream):
-            sh.slab_insert_batch(h, dev(w.keys), dev(w.values), None, stream=stream)
-        torch.cuda.synchronize()
-        ms = []
-        for ops, keys, vals in batches:
-            ms.append(_time_ms(lambda: sh.slab_mixed_batch(h, ops, keys, vals, res, None, stream=stream),
-                               stream, flush))
-        rc, flags = t.status(stream)
-        tot = t.stats()
-        print(json.dumps({"sweep": "mixed", "ratios": ratios, "batches": 64, "batch_ops": N_MIXED,
-                          "unit": "Mops/s", "mean": round(64 * N_MIXED / (sum(ms) * 1e3), 1),
-                          "first_batch": round(N_MIXED / (ms[0] * 1e3), 1),
-                          "last_batch": round(N_MIXED / (ms[-1] * 1e3), 1),
-                          "final_slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4),
-                          "status": rc}), flush=True)
-        t.close()
+            sh.slab_reset(h, stream)
+            sh.slab_insert_batch(h, kb, vb, None, stream=stream)
+        ms_del.append(_time_ms(lambda: sh.slab_delete_batch(h, kd, None, stream=stream), stream, flush))
+    rc, flags = t.status(stream)
+    t.close()
+    line = {"beta": beta, "num_buckets": w.num_buckets, "unit": "Mops/s",
+            "build_incl_reset": round(N_KEYS / (ms_build * 1e3), 1), **rates,
+            "delete": round(N_DELETE / (min(ms_del) * 1e3), 1), "utilization": round(util, 4),
+            "slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4), "status": rc}
+    return line, (w, queries)
+
+
+def bulk_oracle_lines(w, queries, slab_bytes=128):
+    """The oracle's slab reads per op for bulk_point's batches."""
+    from oracle import OracleTable
+    o = OracleTable(w.num_buckets, w.hash_a, w.hash_b, slab_bytes=slab_bytes)
+    o.insert(w.keys, w.values)
+    out = {"build_incl_reset": o.lines / N_KEYS}
+    for hr, q in queries.items():
+        o.lines = 0
+        o.search(q)
+        out[f"search_{int(hr * 100)}"] = o.lines / N_SEARCH
+    o.lines = 0
+    o.delete(w.delete_keys)
+    out["delete"] = o.lines / N_DELETE
+    o.close()
+    return out
+
+
+def mixed_series(args, device, stream, flush, ratios, batches=64):
+    """The concurrent benchmark (Sec. 6.3) at one ratio: preload 2^22 pairs (beta
+    0.6), then `batches` batches of 2^20 mixed ops, each timed alone after an L2
+    flush; tombstones accumulate (no flush of the table). Returns (rates, host
+    inputs for the oracle)."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    dev = sh.as_device_u32
+    w = W.config2(BETA, HIT, args.seed)
+    ks = W.KeyStream(args.seed)
+    ks.take(N_KEYS + N_SEARCH)
+    rng = np.random.default_rng([args.seed, 0xC0C0])
+    live = w.keys
+    host_batches, dev_batches = [], []
+    for _ in range(batches):
+        mb, live = W.mixed_batch(ks, live, N_MIXED, ratios, rng)
+        host_batches.append(mb)
+        dev_batches.append((torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)))
+    t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, 1 << 22)
+    h = t.handle
+    res = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+    with torch.cuda.stream(stream):
+        sh.slab_insert_batch(h, dev(w.keys), dev(w.values), None, stream=stream)
+    torch.cuda.synchronize()
+    ms = []
+    for ops, keys, vals in dev_batches:
+        ms.append(_time_ms(lambda: sh.slab_mixed_batch(h, ops, keys, vals, res, None, stream=stream),
+                           stream, flush))
+    rc, flags = t.status(stream)
+    tot = t.stats()
+    t.close()
+    line = {"ratios": ratios, "batches": batches, "batch_ops": N_MIXED, "unit": "Mops/s",
+            "mean": round(batches * N_MIXED / (sum(ms) * 1e3), 1),
+            "first_batch": round(N_MIXED / (ms[0] * 1e3), 1),
+            "last_batch": round(N_MIXED / (ms[-1] * 1e3), 1),
+            "final_slabs_per_bucket": round(tot["slabs"] / w.num_buckets, 4), "status": rc}
+    return line, (w, host_batches, ms)
+
+
+def mixed_oracle_lines(w, host_batches):
+    """The oracle's slab reads per op, batch by batch, for mixed_series' batches."""
+    from oracle import OracleTable
+    o = OracleTable(w.num_buckets, w.hash_a, w.hash_b)
+    o.insert(w.keys, w.values)
+    per = []
+    for mb in host_batches:
+        o.lines = 0
+        o.mixed(mb.ops, mb.keys, mb.values)
+        per.append(o.lines / len(mb.keys))
+    o.close()
+    return per
 
 
 def slaballoc_sweep(device, stream, flush, reps):
-    """SlabAlloc microbenchmark (Sec. 5)."""
+    """SlabAlloc microbenchmark (Sec. 5), printed as a sweep line."""
+    print(json.dumps({"sweep": "slaballoc", **slaballoc_point(device, stream, flush, reps)}), flush=True)
+
+
+def slaballoc_point(device, stream, flush, reps):
+    """SlabAlloc microbenchmark (Sec. 5): 2^24 single-slab allocations (one per lane,
+    batched and one at a time), 2^24 frees, against a random 32-bit atomicOr probe
+    on a bitmap region of the same size."""
     import torch
 
     from paper_1710_11246_gb300 import slabhash as sh
@@ -661,14 +730,14 @@ def slaballoc_sweep(device, stream, flush, reps):
                                stream, flush))
         or_rate = max(or_rate, n / (min(ms) * 1e-3))
     del bm
-    print(json.dumps({"sweep": "slaballoc", "allocations": n, "pool_slabs": 1 << 25, "unit": "Mops/s",
-                      "alloc": round(n / (min(a_ms) * 1e3), 1), "free": round(n / (min(f_ms) * 1e3), 1),
-                      "alloc_one_at_a_time": round(n / (min(a1_ms) * 1e3), 1),
-                      "random_atomic_or_bitmap": round(or_rate / 1e6, 1),
-                      "alloc_frac_of_atomic_rate": round(n / (min(a_ms) * 1e-3) / or_rate, 4),
-                      "status": rc, "bitmaps_clear_after_free": bm_zero}), flush=True)
     t.close()
     del addrs
+    return {"allocations": n, "pool_slabs": 1 << 25, "unit": "Mops/s",
+            "alloc": round(n / (min(a_ms) * 1e3), 1), "free": round(n / (min(f_ms) * 1e3), 1),
+            "alloc_one_at_a_time": round(n / (min(a1_ms) * 1e3), 1),
+            "random_atomic_or_bitmap": round(or_rate / 1e6, 1),
+            "alloc_frac_of_atomic_rate": round(n / (min(a_ms) * 1e-3) / or_rate, 4),
+            "status": rc, "bitmaps_clear_after_free": bm_zero}
 
 
 
@@ -1005,6 +1074,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the config-2 / config-3 / 64-byte keys of the step line")
     ap.add_argument("--sweep", nargs="?", const="all", default=None,
                     choices=["all", "bulk", "slaballoc", "learned", "group", "serving", "flush", "sizes", "incremental",
                              "mixed"],
@@ -1099,6 +1170,9 @@ def main():
                                    " both probed live at the table's footprint (of measured)",
                     "lines_per_op": {p: round(lines[p] / ops[p], 4) for p in ops},
                     "hbm_view": hbm_view}
+    sweeps = None
+    if world == 1 and rl is not None and not args.no_extras:
+        sweeps = extras(args, device, (rl["glines_per_s"] * 1e9, rl["gcas_per_s"] * 1e9))
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mops/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
@@ -1108,12 +1182,141 @@ def main():
         "per_op_source": "instrumented pass: CUDA events between every phase, K steps after the timed ones",
         "dominant_kernel_ms_timed": round(dom_mean, 4),
         "roofline": roof, "random_line_roofline": rl, "cpu_baseline": cpu,
-        "e2e": r["e2e"], "gpu_launches": 5 * args.steps, "clocks": r["clocks"],
+        "e2e": r["e2e"], "gpu_launches": 5 * args.steps, "clocks": r["clocks"], "sweeps": sweeps,
     }
     print(json.dumps(out))
     r["table"].close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def width_step(args, device, slab_bytes):
+    """The benchmark step (reset, build, search, delete, mixed) on a table of
+    `slab_bytes` slabs at the same beta (B = ceil(n / (M beta)) with M pairs per
+    slab), L2 flushed before every step, CUDA events between phases, K steps after
+    W warm-up steps. Returns (per-phase results, host inputs for the oracle)."""
+    import torch
+
+    from paper_1710_11246_gb300 import slabhash as sh
+    per = (slab_bytes // 4 - 2) // 2
+    w, mb = make_step_inputs(args.seed, per_slab=per)
+    dev = sh.as_device_u32
+    t = sh.SlabHash(w.num_buckets, w.hash_a, w.hash_b, POOL_SLABS, slab_bytes=slab_bytes)
+    h = t.handle
+    stream = torch.cuda.Stream()
+    k_build, v_build, k_search, k_del = dev(w.keys), dev(w.values), dev(w.search.keys), dev(w.delete_keys)
+    m_ops, m_keys, m_vals = torch.from_numpy(mb.ops).to(device), dev(mb.keys), dev(mb.values)
+    o_search = torch.empty(N_SEARCH, dtype=torch.int32, device=device)
+    f_search = torch.empty(N_SEARCH, dtype=torch.uint8, device=device)
+    f_del = torch.empty(N_DELETE, dtype=torch.uint8, device=device)
+    o_mixed = torch.empty(N_MIXED, dtype=torch.int32, device=device)
+    f_mixed = torch.empty(N_MIXED, dtype=torch.uint8, device=device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    calls = (lambda: sh.slab_reset(h, stream),
+             lambda: sh.slab_insert_batch(h, k_build, v_build, None, stream=stream),
+             lambda: sh.slab_search_batch(h, k_search, o_search, f_search, stream=stream),
+             lambda: sh.slab_delete_batch(h, k_del, f_del, stream=stream),
+             lambda: sh.slab_mixed_batch(h, m_ops, m_keys, m_vals, o_mixed, f_mixed, stream=stream))
+    all_evs = []
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            for j, c in enumerate(calls):
+                evs[j].record(stream)
+                c()
+            evs[5].record(stream)
+            if i >= args.warmup:
+                all_evs.append(evs)
+    torch.cuda.synchronize()
+    rc, flags = t.status(stream)
+    if rc != sh.SLAB_OK:
+        raise RuntimeError(f"{slab_bytes}-byte step: device status rc={rc} flags={flags}")
+    ok = int(f_search.sum().item()) == int(w.search.present.sum()) and bool((f_del == 1).all().item())
+    t.close()
+    mean = {p: statistics.fmean(e[i].elapsed_time(e[i + 1]) for e in all_evs) for i, p in enumerate(PHASES)}
+    ops = {"build": N_KEYS, "search": N_SEARCH, "delete": N_DELETE, "mixed": N_MIXED}
+    res = {"slab_bytes": slab_bytes, "pairs_per_slab": per, "num_buckets": w.num_buckets, "beta": BETA,
+           "steps": args.steps, "per_op_mops": {p: round(ops[p] / (mean[p] * 1e3), 1) for p in ops},
+           "phase_ms": {p: round(mean[p], 4) for p in PHASES}, "results_checked": ok}
+    return res, (w, mb)
+
+
+def line_cas_fracs(rates_mops, lines_per_op, cas_per_op, line_rate, cas_rate):
+    """Each phase's rate as a fraction of min(line rate / lines per op, CAS rate / CAS per op)."""
+    out = {}
+    for p, r in rates_mops.items():
+        if p not in lines_per_op:
+            continue
+        bound = min(line_rate / lines_per_op[p], cas_rate / cas_per_op[p] if cas_per_op.get(p) else float("inf"))
+        out[p] = round(r * 1e6 / bound, 4)
+    return out
+
+
+def extras(args, device, main_rates):
+    """Configs 2 and 3 and the 64-byte slab width as keys of the step's line: the
+    bulk benchmark over beta at 0 / 50 / 100 % hit (Sec. 6.1), the SlabAlloc
+    microbenchmark (Sec. 5), 64 concurrent batches at each ratio (Sec. 6.3) and the
+    step on 64-byte slabs, each figure with its fraction of the random-line / CAS
+    bound at its table's footprint. The oracle's line counts run in threads beside
+    the GPU work (the C oracle releases the interpreter lock)."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    ex = ThreadPoolExecutor(max_workers=max(2, min(8, (os.cpu_count() or 4) - 1)))
+    t0 = time.perf_counter()
+
+    bulk = []
+    for beta in W.CONFIG2_BETAS:
+        line, (w, queries) = bulk_point(args, device, stream, flush, beta, reps=3)
+        fut = ex.submit(bulk_oracle_lines, w, queries)
+        fp = w.num_buckets * 128
+        lr, _ = random_line_probe(device, fp, quick=True)
+        cr, _ = random_cas_probe(device, fp, quick=True)
+        bulk.append((line, fut, lr, cr))
+    slaballoc = slaballoc_point(device, stream, flush, 3)
+    series = []
+    for ratios in W.CONFIG3_RATIOS:
+        line, (w, hb, ms) = mixed_series(args, device, stream, flush, ratios)
+        ins = [float((mb.ops == W.OP_INSERT).mean()) for mb in hb]
+        series.append((line, ex.submit(mixed_oracle_lines, w, hb), ins, ms))
+    s64, (w64, mb64) = width_step(args, device, 64)
+    fut64 = ex.submit(run_oracle_step, w64, mb64, 64)
+    lr64, cfg64 = random_line_probe(device, w64.num_buckets * 64, line_bytes=64, quick=True)
+    cr64, _ = random_cas_probe(device, w64.num_buckets * 64, quick=True)
+
+    out = {"config2_beta_sweep": [], "slaballoc_2e24": slaballoc, "config3_concurrent": []}
+    for line, fut, lr, cr in bulk:
+        lines = fut.result()
+        rates = {k: line[k] for k in lines}
+        line["lines_per_op"] = {k: round(v, 4) for k, v in lines.items()}
+        line["glines_per_s"], line["gcas_per_s"] = round(lr / 1e9, 2), round(cr / 1e9, 2)
+        line["frac_line_cas"] = line_cas_fracs(rates, lines, {"build_incl_reset": 1.0}, lr, cr)
+        out["config2_beta_sweep"].append(line)
+    lr3, cr3 = main_rates
+    for line, fut, ins, ms in series:
+        per = fut.result()
+        fr = []
+        for lpo, fi, m in zip(per, ins, ms):
+            bound = min(lr3 / lpo, cr3 / fi if fi else float("inf"))
+            fr.append(N_MIXED / (m * 1e-3) / bound)
+        line["lines_per_op_first_last"] = [round(per[0], 4), round(per[-1], 4)]
+        line["frac_line_cas"] = {"mean": round(statistics.fmean(fr), 4), "first_batch": round(fr[0], 4),
+                                 "last_batch": round(fr[-1], 4)}
+        out["config3_concurrent"].append(line)
+    _, lines64, _ = fut64.result()
+    ops = {"build": N_KEYS, "search": N_SEARCH, "delete": N_DELETE, "mixed": N_MIXED}
+    lpo64 = {p: lines64[p] / ops[p] for p in ops}
+    cas64 = {"build": 1.0, "mixed": float((mb64.ops == W.OP_INSERT).mean())}
+    s64["lines_per_op"] = {p: round(v, 4) for p, v in lpo64.items()}
+    s64["random_64B_line_roofline"] = {"footprint_bytes": w64.num_buckets * 64, "glines_per_s": round(lr64 / 1e9, 2),
+                                       "probe": cfg64, "gcas_per_s": round(cr64 / 1e9, 2)}
+    s64["frac_line_cas"] = line_cas_fracs(s64["per_op_mops"], lpo64, cas64, lr64, cr64)
+    out["slab64_step"] = s64
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    ex.shutdown()
+    return out
 
 
 def reference_arm(args, rank, world):
