@@ -827,10 +827,16 @@ def group_sweep(args, device, stream, flush):
     rc, _ = sh.slab_group_status(g, stream)
     line["status"] = rc
     sh.slab_group_destroy(g)
+    g64 = AT.create_group(gw, BETA, 64)
+    line["group_launch_64B_slabs"] = round(ops / (AT.time_group(g64, arrays, gout, gfnd, stream) * 1e3), 1)
+    sh.slab_group_destroy(g64)
     best, cands = AT.tune_group(gw, device=device)
-    line["autotuned"] = {"beta": best.beta, "threads_per_block": best.threads_per_block,
+    line["autotuned"] = {"slab_bytes": best.slab_bytes, "beta": best.beta,
+                         "threads_per_block": best.threads_per_block,
                          "blocks_per_sm": best.blocks_per_sm, "mops": round(best.mops, 1),
                          "candidates": len(cands),
+                         "best_per_width": {w: round(max(c.mops for c in cands if c.slab_bytes == w), 1)
+                                            for w in sorted({c.slab_bytes for c in cands})},
                          "worst_mops": round(min(c.mops for c in cands), 1)}
     print(json.dumps(line), flush=True)
 

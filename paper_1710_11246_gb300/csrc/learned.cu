@@ -10,6 +10,7 @@
 // the same model bit for bit.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/slabhash.h"
@@ -82,71 +83,144 @@ __global__ void sample_kernel(const uint32_t* keys, uint32_t stride, uint32_t m,
         sample[i] = i < m ? keys[(uint64_t)i * stride] : 0xFFFFFFFFu;
 }
 
-// Ascending bitonic sort of p (a power of two) words by one block.
-__global__ void bitonic_sort_kernel(uint32_t* v, uint32_t p) {
-    for (uint32_t k = 2; k <= p; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < p; i += blockDim.x) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint32_t x = v[i], y = v[ixj];
-                    const bool ascending = (i & k) == 0;
-                    if ((x > y) == ascending) {
-                        v[i] = y;
-                        v[ixj] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+// Ascending bitonic sort of p (a power of two) words over many blocks. The
+// network's compare-exchange stages with partner distance j >= kSortTile / 2 run
+// one launch each over global memory (bitonic_global_kernel); every run of stages
+// with smaller distances works inside aligned tiles of kSortTile words, so it runs
+// as one launch that sorts each tile's part in shared memory (bitonic_tile_kernel).
+constexpr uint32_t kSortTile = 2048;  // words per shared-memory tile (two per thread)
+
+__device__ __forceinline__ void compare_exchange(uint32_t& x, uint32_t& y, bool ascending) {
+    if ((x > y) == ascending) {
+        const uint32_t t = x;
+        x = y;
+        y = t;
     }
 }
 
-// One block. Root: fit leaf position i * 1024 / m against the i-th smallest sample
-// key. Leaf j: the sample points the root sends to j (a contiguous run, since every
-// fitted slope is >= 0) fit bucket position i * B / m; a leaf with no point is flat
-// at the position where its run would start.
-__global__ void __launch_bounds__(kFitThreads) fit_kernel(const uint32_t* sorted, uint32_t m, uint32_t num_buckets,
-                                                          float* model) {
-    __shared__ Moments part[kFitThreads];
-    __shared__ float root[2];
-    const uint32_t tid = threadIdx.x;
-    Moments mo{};
-    for (uint32_t i = tid; i < m; i += kFitThreads) add_point(mo, sorted[i], (unsigned long long)i * kLeaves);
-    part[tid] = mo;
-    __syncthreads();
-    if (tid == 0) {
-        Moments all{};
-        for (int k = 0; k < kFitThreads; ++k) {
-            all.n += part[k].n;
-            all.sx += part[k].sx;
-            all.sy += part[k].sy;
-            all.sxx += part[k].sxx;
-            all.sxy += part[k].sxy;
-        }
-        fit_line(all, m, &root[0], &root[1]);
-        model[0] = root[0];
-        model[1] = root[1];
+// Stage (k, j) of the network for all pairs (i, i ^ j), j >= kSortTile / 2.
+__global__ void bitonic_global_kernel(uint32_t* v, uint32_t p, uint32_t k, uint32_t j) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < p / 2; t += gridDim.x * blockDim.x) {
+        const uint32_t i = (t / j) * 2u * j + (t % j);  // the lower index of pair t
+        uint32_t x = v[i], y = v[i + j];
+        compare_exchange(x, y, (i & k) == 0);
+        v[i] = x;
+        v[i + j] = y;
     }
+}
+
+// Stages (k, j) for j = j0, j0 / 2, ..., 1 of one merge size k (or, with
+// k0 = 0, every stage of every k <= kSortTile) inside each tile of kSortTile words.
+__global__ void __launch_bounds__(kSortTile / 2) bitonic_tile_kernel(uint32_t* v, uint32_t k_fixed, uint32_t j0) {
+    __shared__ uint32_t sm[kSortTile];
+    const uint32_t base = blockIdx.x * kSortTile;
+    for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) sm[i] = v[base + i];
     __syncthreads();
-    const float ra = root[0], rb = root[1];
+    auto run = [&](uint32_t k, uint32_t jstart) {
+        for (uint32_t j = jstart; j > 0; j >>= 1) {
+            const uint32_t t = threadIdx.x;  // pair t of the tile's kSortTile / 2
+            const uint32_t i = (t / j) * 2u * j + (t % j);
+            uint32_t x = sm[i], y = sm[i + j];
+            compare_exchange(x, y, ((base + i) & k) == 0);
+            sm[i] = x;
+            sm[i + j] = y;
+            __syncthreads();
+        }
+    };
+    if (k_fixed == 0) {
+        for (uint32_t k = 2; k <= kSortTile; k <<= 1) run(k, k >> 1);
+    } else {
+        run(k_fixed, j0);
+    }
+    for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) v[base + i] = sm[i];
+}
+
+// Sort p words (a power of two) ascending: a sequence of launches on `s`.
+void bitonic_sort(uint32_t* v, uint32_t p, cudaStream_t s, const slab_table* t) {
+    if (p <= kSortTile) {  // one tile: one block of the tile kernel on a padded copy is not needed
+        // p < kSortTile only for tiny samples; run the global stages, which cover any p
+        for (uint32_t k = 2; k <= p; k <<= 1)
+            for (uint32_t j = k >> 1; j > 0; j >>= 1)
+                bitonic_global_kernel<<<util_grid(t, p / 2, 256), 256, 0, s>>>(v, p, k, j);
+        return;
+    }
+    const uint32_t tiles = p / kSortTile;
+    bitonic_tile_kernel<<<tiles, kSortTile / 2, 0, s>>>(v, 0u, 0u);
+    for (uint32_t k = 2 * kSortTile; k <= p; k <<= 1) {
+        for (uint32_t j = k >> 1; j >= kSortTile / 2 * 2; j >>= 1)
+            bitonic_global_kernel<<<util_grid(t, p / 2, 256), 256, 0, s>>>(v, p, k, j);
+        bitonic_tile_kernel<<<tiles, kSortTile / 2, 0, s>>>(v, k, kSortTile / 2);
+    }
+}
+
+__device__ void add_moments(Moments& a, const Moments& b) {
+    a.n += b.n;
+    a.sx += b.sx;
+    a.sy += b.sy;
+    a.sxx += b.sxx;
+    a.sxy += b.sxy;
+}
+
+// The block's exact moments summed into part[0] (integer sums: the order of the
+// additions does not change the result).
+__device__ void block_moments(Moments mine, Moments* part) {
+    part[threadIdx.x] = mine;
+    __syncthreads();
+    for (uint32_t o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) add_moments(part[threadIdx.x], part[threadIdx.x + o]);
+        __syncthreads();
+    }
+}
+
+// Root, part 1: block b's moments of the points (sorted[i], i * 1024), i < m.
+__global__ void __launch_bounds__(kFitThreads) root_moments_kernel(const uint32_t* sorted, uint32_t m,
+                                                                   Moments* partial) {
+    __shared__ Moments part[kFitThreads];
+    Moments mo{};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        add_point(mo, sorted[i], (unsigned long long)i * kLeaves);
+    block_moments(mo, part);
+    if (threadIdx.x == 0) partial[blockIdx.x] = part[0];
+}
+
+// Root, part 2 (one block): the root line from the blocks' moments: leaf position
+// i * 1024 / m fitted against the i-th smallest sample key.
+__global__ void __launch_bounds__(kFitThreads) root_fit_kernel(const Moments* partial, uint32_t nparts, uint32_t m,
+                                                               float* model) {
+    __shared__ Moments part[kFitThreads];
+    Moments mo{};
+    for (uint32_t b = threadIdx.x; b < nparts; b += blockDim.x) add_moments(mo, partial[b]);
+    block_moments(mo, part);
+    if (threadIdx.x == 0) fit_line(part[0], m, &model[0], &model[1]);
+}
+
+// Leaves, one block per leaf j: the sample points the root sends to j (a
+// contiguous run, since the root's slope is >= 0) fit bucket position i * B / m;
+// a leaf with no point is flat at the position where its run would start.
+__global__ void __launch_bounds__(kFitThreads) leaf_fit_kernel(const uint32_t* sorted, uint32_t m,
+                                                               uint32_t num_buckets, float* model) {
+    __shared__ Moments part[kFitThreads];
+    const uint32_t j = blockIdx.x;
+    const float ra = model[0], rb = model[1];
     auto leaf_of = [&](uint32_t i) { return linear_piece(ra, rb, __uint2float_rn(sorted[i]), kLeaves); };
-    auto first_at_least = [&](uint32_t j) {  // smallest i with leaf_of(i) >= j, or m
+    auto first_at_least = [&](uint32_t jj) {  // smallest i with leaf_of(i) >= jj, or m
         uint32_t lo = 0, hi = m;
         while (lo < hi) {
             const uint32_t mid = lo + (hi - lo) / 2;
-            if (leaf_of(mid) >= j) hi = mid;
+            if (leaf_of(mid) >= jj) hi = mid;
             else lo = mid + 1;
         }
         return lo;
     };
-    for (uint32_t j = tid; j < kLeaves; j += kFitThreads) {
-        const uint32_t lo = first_at_least(j), hi = first_at_least(j + 1);
+    const uint32_t lo = first_at_least(j), hi = first_at_least(j + 1);
+    Moments lm{};
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        add_point(lm, sorted[i], (unsigned long long)i * num_buckets);
+    block_moments(lm, part);
+    if (threadIdx.x == 0) {
         float a = 0.0f, b;
         if (hi > lo) {
-            Moments lm{};
-            for (uint32_t i = lo; i < hi; ++i) add_point(lm, sorted[i], (unsigned long long)i * num_buckets);
-            fit_line(lm, m, &a, &b);
+            fit_line(part[0], m, &a, &b);
         } else {
             b = __double2float_rn(__ddiv_rn(__ull2double_rn((unsigned long long)lo * num_buckets),
                                             __ull2double_rn(m)));
@@ -202,22 +276,29 @@ int slab_learn_buckets(slab_table* t, const uint32_t* d_keys, uint32_t n, uint32
     while (p < m) p <<= 1;
     const cudaStream_t s = S(stream);
     const uint64_t B = t->num_buckets;
-    // scratch: padded sample, per-bucket counts, two sums and two maxima
+    // scratch: padded sample, per-bucket counts, two sums and two maxima, the root's
+    // per-block moments
+    constexpr uint32_t kRootParts = 512;
     char* scratch = nullptr;
-    const size_t bytes = (size_t)p * 4 + (size_t)B * 4 + 32;
+    const size_t moments_at = (((size_t)p + B) * 4 + 32 + 15) / 16 * 16;
+    const size_t bytes = moments_at + kRootParts * sizeof(Moments);
     if (cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s) != cudaSuccess) return SLAB_ERR_CUDA;
     uint32_t* sample = reinterpret_cast<uint32_t*>(scratch);
     uint32_t* counts = sample + p;
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(scratch + (((size_t)p + B) * 4 + 7) / 8 * 8);
     uint32_t* maxima = reinterpret_cast<uint32_t*>(sums + 2);
+    Moments* root_parts = reinterpret_cast<Moments*>(scratch + moments_at);
     int rc = SLAB_OK;
     unsigned long long h_sums[2] = {0, 0};
     uint32_t h_max[2] = {0, 0};
     const uint32_t per_slab = t->mode == SLAB_MODE_KEY_ONLY ? t->slab_words - 2u : (t->slab_words - 2u) / 2u;
     do {
         sample_kernel<<<util_grid(t, p, 256), 256, 0, s>>>(d_keys, sample_stride, m, p, sample);
-        bitonic_sort_kernel<<<1, 1024, 0, s>>>(sample, p);
-        fit_kernel<<<1, kFitThreads, 0, s>>>(sample, m, t->num_buckets, t->d_model);
+        bitonic_sort(sample, p, s, t);
+        const uint32_t parts = std::min<uint32_t>(kRootParts, (m + kFitThreads - 1) / kFitThreads);
+        root_moments_kernel<<<parts, kFitThreads, 0, s>>>(sample, m, root_parts);
+        root_fit_kernel<<<1, kFitThreads, 0, s>>>(root_parts, parts, m, t->d_model);
+        leaf_fit_kernel<<<kLeaves, kFitThreads, 0, s>>>(sample, m, t->num_buckets, t->d_model);
         if ((rc = launch_rc()) != SLAB_OK) break;
         if (cudaMemsetAsync(sums, 0, 24, s) != cudaSuccess) { rc = SLAB_ERR_CUDA; break; }
         TableView T = view(t);

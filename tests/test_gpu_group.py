@@ -144,3 +144,37 @@ def test_group_in_cuda_graph():
         assert rc == sh.SLAB_OK
     finally:
         sh.slab_group_destroy(g)
+
+
+def test_autotuner_searches_slab_width():
+    """The autotuner times every (slab width, beta, launch shape) candidate on the
+    group's own step and returns the fastest; the chosen configuration, rebuilt,
+    still matches each table's oracle at its width."""
+    from oracle import OracleTable
+    from paper_1710_11246_gb300 import autotune as AT
+    gw = W.group_workload(24, 1 << 6, 1 << 12, seed=12)
+    best, cands = AT.tune_group(gw, betas=(0.6, 1.0), threads=(64, 128), blocks=(0,), widths=(128, 64), reps=1)
+    assert {c.slab_bytes for c in cands} == {128, 64} and len(cands) == 8
+    assert best.mops == max(c.mops for c in cands) and all(c.ms > 0 for c in cands)
+    g = AT.create_group(gw, best.beta, best.slab_bytes)
+    try:
+        cfg = sh.slab_group_get_config(g)
+        cfg.threads_per_block, cfg.blocks_per_sm = best.threads_per_block, best.blocks_per_sm
+        sh.slab_group_set_config(g, cfg)
+        st, k, v, qs, q = AT._arrays(gw, "cuda")
+        out = torch.empty(len(gw.search_keys), dtype=torch.int32, device="cuda")
+        fnd = torch.empty(len(gw.search_keys), dtype=torch.uint8, device="cuda")
+        AT.group_step(g, (st, k, v, qs, q), out, fnd, None)
+        torch.cuda.synchronize()
+        gv, gf = sh.to_host_u32(out), fnd.cpu().numpy()
+        per = (best.slab_bytes // 4 - 2) // 2
+        for i in range(24):
+            lo, hi = int(gw.op_start[i]), int(gw.op_start[i + 1])
+            o = OracleTable(W.buckets_for(max(int(gw.sizes[i]), 1), best.beta, per), int(gw.hash_a[i]),
+                            int(gw.hash_b[i]), slab_bytes=best.slab_bytes)
+            o.insert(gw.keys[lo:hi], gw.values[lo:hi])
+            ov, of = o.search(gw.search_keys[lo:hi])
+            assert (ov == gv[lo:hi]).all() and (of == gf[lo:hi]).all()
+            o.close()
+    finally:
+        sh.slab_group_destroy(g)

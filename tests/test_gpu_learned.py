@@ -127,3 +127,28 @@ def test_full_size_clustered_model_and_report():
         assert tot["live"] == len(w.keys) and tot["prefix_violations"] == 0
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("n,stride,slab_bytes", [(1 << 26, 100, 128), (3 << 20, 3, 128), (1 << 20, 100, 64)])
+def test_fit_scales_to_the_serving_table(n, stride, slab_bytes):
+    """The multi-block sort and fit at the serving table's size (2^26 keys, a 1 %
+    sample of 671,089 keys padded to 2^20), at the largest sample the call takes
+    (2^20 keys: a 3 x 2^20-key set at stride 3) and on a 64-byte table: the model
+    and its chain profile match the oracle's bit for bit."""
+    keys = W.KeyStream(n + stride).take(n)
+    B = W.buckets_for(n, 0.6, (slab_bytes // 4 - 2) // 2)
+    t = sh.SlabHash(B, 5, 7, 1024, slab_bytes=slab_bytes)
+    try:
+        rep = sh.slab_learn_buckets(t.handle, dev(keys), stride, sh.SLAB_LEARN_MEASURE)
+        model_g, in_use = sh.slab_get_model(t.handle)
+        model_o, m = learn_model(keys, stride, B)
+        assert rep["sample_size"] == m and not in_use
+        assert model_g.view(np.uint32).tolist() == model_o.view(np.uint32).tolist(), \
+            np.flatnonzero(model_g.view(np.uint32) != model_o.view(np.uint32))[:8]
+        o = OracleTable(B, 5, 7, slab_bytes=slab_bytes)
+        o.use_model(model_o)
+        s, mx = o.chain_profile(keys)
+        assert rep["max_slabs_learned"] == mx and abs(rep["mean_slabs_learned"] - s / B) < 1e-12
+        o.close()
+    finally:
+        t.close()
