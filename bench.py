@@ -335,11 +335,12 @@ def gpu_arm(args, rank, world, device):
 
 
 def e2e_arm(args, t, w, mb, device, stream):
-    """End to end through the C ABI from page-locked host buffers: every step copies
-    all its inputs to the device and all its results back inside the timed region.
-    Copies in, batches and copies out run on three streams ordered by events, and
-    the device buffers alternate between two sets, so a step's input copies overlap
-    the previous step's batches and its result copies overlap the batches that follow."""
+    """End to end through the C ABI's host-memory batch call (slab_batch_host): every
+    step passes page-locked host arrays of all its inputs and gets all its results
+    back in host arrays. The library copies each chunk in and its results out on
+    its own copy streams, overlapping the kernels of the neighbouring chunks; each
+    call records a completion event instead of making the kernel stream wait for
+    its copies, so a step's copies also overlap the next step's batches."""
     import torch
 
     from paper_1710_11246_gb300 import slabhash as sh
@@ -349,82 +350,39 @@ def e2e_arm(args, t, w, mb, device, stream):
                mk=pin(mb.keys), mv=pin(mb.values))
     out_shapes = [(N_SEARCH, torch.int32), (N_SEARCH, torch.uint8), (N_DELETE, torch.uint8), (N_MIXED, torch.int32),
                   (N_MIXED, torch.uint8)]
-    sets = []
-    for _ in range(2):
-        sets.append(dict(d={n: torch.empty_like(x, device=device) for n, x in hin.items()},
-                         dout=[torch.empty(n, dtype=dt, device=device) for n, dt in out_shapes],
-                         hout=[torch.empty(n, dtype=dt).pin_memory() for n, dt in out_shapes],
-                         inputs_free=None, outputs_free=None))
+    hout = [torch.empty(n, dtype=dt).pin_memory() for n, dt in out_shapes]
     h2d = sum(x.numel() * x.element_size() for x in hin.values())
-    d2h = sum(n * torch.tensor([], dtype=dt).element_size() for n, dt in out_shapes)
-    cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
+    d2h = sum(x.numel() * x.element_size() for x in hout)
     ks = stream
 
-    def mark(st):
-        e = torch.cuda.Event()
-        e.record(st)
-        return e
-
-    def one(i):
-        S = sets[i % 2]
-        d, dout, hout = S["d"], S["dout"], S["hout"]
-        with torch.cuda.stream(cin):
-            if S["inputs_free"] is not None:  # the batches of two steps ago have read this set
-                cin.wait_event(S["inputs_free"])
-            d["k"].copy_(hin["k"], non_blocking=True)
-            d["v"].copy_(hin["v"], non_blocking=True)
-            e_build = mark(cin)
-            d["s"].copy_(hin["s"], non_blocking=True)
-            e_search = mark(cin)
-            d["dl"].copy_(hin["dl"], non_blocking=True)
-            e_delete = mark(cin)
-            for n in ("ops", "mk", "mv"):
-                d[n].copy_(hin[n], non_blocking=True)
-            e_mixed = mark(cin)
-        ks.wait_event(e_build)
-        if S["outputs_free"] is not None:  # this set's results of two steps ago are on the host
-            ks.wait_event(S["outputs_free"])
+    def one(last_event=None):
         sh.slab_reset(h, ks)
-        sh.slab_insert_batch(h, d["k"], d["v"], None, stream=ks)
-        ks.wait_event(e_search)
-        sh.slab_search_batch(h, d["s"], dout[0], dout[1], stream=ks)
-        r_search = mark(ks)
-        ks.wait_event(e_delete)
-        sh.slab_delete_batch(h, d["dl"], dout[2], stream=ks)
-        r_delete = mark(ks)
-        ks.wait_event(e_mixed)
-        sh.slab_mixed_batch(h, d["ops"], d["mk"], d["mv"], dout[3], dout[4], stream=ks)
-        r_mixed = mark(ks)
-        S["inputs_free"] = r_mixed
-        with torch.cuda.stream(cout):
-            cout.wait_event(r_search)
-            hout[0].copy_(dout[0], non_blocking=True)
-            hout[1].copy_(dout[1], non_blocking=True)
-            cout.wait_event(r_delete)
-            hout[2].copy_(dout[2], non_blocking=True)
-            cout.wait_event(r_mixed)
-            hout[3].copy_(dout[3], non_blocking=True)
-            hout[4].copy_(dout[4], non_blocking=True)
-            S["outputs_free"] = mark(cout)
+        sh.slab_batch_host(h, sh.SLAB_BATCH_INSERT, hin["k"], values=hin["v"], stream=ks, done_event=torch.cuda.Event())
+        sh.slab_batch_host(h, sh.SLAB_BATCH_SEARCH, hin["s"], results=hout[0], found=hout[1], stream=ks,
+                           done_event=torch.cuda.Event())
+        sh.slab_batch_host(h, sh.SLAB_BATCH_DELETE, hin["dl"], found=hout[2], stream=ks, done_event=torch.cuda.Event())
+        sh.slab_batch_host(h, sh.SLAB_BATCH_MIXED, hin["mk"], ops=hin["ops"], values=hin["mv"], results=hout[3],
+                           found=hout[4], stream=ks, done_event=last_event or torch.cuda.Event())
 
     steps = max(3, min(args.steps, 20))
-    for i in range(args.warmup):
-        one(i)
+    for _ in range(args.warmup):
+        one()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(cin)
+    e0.record(ks)
     for i in range(steps):
-        one(args.warmup + i)
-    e1.record(cout)
+        one(e1 if i == steps - 1 else None)
+    e1.synchronize()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     # the last step's results on the host: every present key found, every delete hit
-    last = sets[(args.warmup + steps - 1) % 2]["hout"]
-    if int(last[1].sum()) != int(w.search.present.sum()) or not bool((last[2] == 1).all()):
+    if int(hout[1].sum()) != int(w.search.present.sum()) or not bool((hout[2] == 1).all()):
         raise RuntimeError("end-to-end results on the host disagree with the workload")
     return {"value": round(OPS_PER_STEP / (ms * 1e3), 1), "unit": "Mops/s", "ms_per_step": round(ms, 4),
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "overlap": "copies in, batches and copies out on three streams; two alternating device buffer sets"}
+            "api": "slab_batch_host (host arrays in, host arrays out, default chunks of 2^22 ops)",
+            "overlap": "each chunk's copies overlap the neighbouring chunks' kernels; completion events let a "
+                       "step's copies overlap the next step's batches"}
 
 
 def random_line_probe(device, footprint_bytes: int, n_reads: int = 1 << 24, line_bytes: int = 128,

@@ -532,6 +532,40 @@ int slab_server_run(slab_server *sv, uint64_t n_requests, const uint64_t *h_arri
                     uint8_t *h_found, uint64_t *h_latency_ns, uint64_t *h_wait_ns, uint8_t *h_status,
                     uint64_t *h_makespan_ns);
 
+/*
+ * A batch whose arrays live in host memory (a library service around the batch
+ * calls above; the paper's batches start in device memory). kind is one of
+ * enum slab_batch_kind; the arrays are those of the matching device call, in host
+ * memory: h_keys (all kinds), h_values (insert and mixed; ignored in key-only
+ * mode, required for inserts in key-value mode), h_ops (mixed), h_results
+ * (search values, mixed results; not used by insert or delete), h_found
+ * (nullable). Page-locked arrays (cudaHostAlloc, or pinned torch tensors) move at
+ * the host link's full rate and leave the call asynchronous; pageable arrays
+ * work, but their copies block the calling thread.
+ * The call splits the batch into chunks of `chunk` ops (0: 2^22) and runs them in
+ * order: each chunk's inputs are copied to device staging buffers owned by the
+ * table (a ring of four sets of min(chunk, n) ops, 14 bytes per op each, made on
+ * the first call and remade larger when a call needs more, which waits for the
+ * device),
+ * its batch runs on `stream`, and its results are copied back, the copies of one
+ * chunk overlapping the kernels of its neighbours on internal copy streams. The
+ * results equal those of the whole batch run at once: each key appears in at most
+ * one op of a batch, and ops on distinct keys commute.
+ * Completion: with done_event = NULL, `stream` completes only once every result
+ * is in host memory (so a following batch on `stream` waits for these copies);
+ * with a cudaEvent_t, the call records it after its last copy back and `stream`
+ * does not wait for the copies, so the next batch can overlap them; the results
+ * are in host memory once the event has completed. The host arrays must stay
+ * valid until then. Not safe for concurrent calls on one table.
+ * Errors: SLAB_ERR_INVALID_ARG for a bad kind or a missing required array;
+ * SLAB_ERR_CUDA if staging cannot be allocated or a copy cannot be queued; the
+ * device status word as for the device calls. n = 0 is a no-op.
+ */
+enum slab_batch_kind { SLAB_BATCH_INSERT = 0, SLAB_BATCH_DELETE = 1, SLAB_BATCH_SEARCH = 2, SLAB_BATCH_MIXED = 3 };
+int slab_batch_host(slab_table *t, int kind, const uint8_t *h_ops, const uint32_t *h_keys, const uint32_t *h_values,
+                    uint32_t *h_results, uint8_t *h_found, uint32_t n, uint32_t chunk, void *stream,
+                    void *done_event);
+
 /* Human-readable name of a return code. Never NULL. */
 const char *slab_error_string(int rc);
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libslabhash.so")
-SOURCES = ["slabhash.cu", "probe.cu", "learned.cu", "group.cu", "server.cu", "variants.cu"]
+SOURCES = ["slabhash.cu", "probe.cu", "learned.cu", "group.cu", "server.cu", "variants.cu", "host_batch.cu"]
 HEADERS = ["slab_device.cuh", "slab_wcws.cuh", "slab_staged.cuh", "slab_table.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"] + ARCH

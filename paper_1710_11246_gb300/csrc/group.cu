@@ -364,7 +364,10 @@ int slab_group_create(uint32_t ntables, const uint32_t* h_num_buckets, const uin
 void slab_group_destroy(slab_group* g) {
     if (!g) return;
     cudaDeviceSynchronize();
-    for (slab_table* t : g->tables) delete t;
+    for (slab_table* t : g->tables) {
+        slab_host::free_host_io(t);
+        delete t;
+    }
     cudaFree(g->d_arena);
     cudaFree(g->d_views);
     cudaFree(g->d_tile_start);

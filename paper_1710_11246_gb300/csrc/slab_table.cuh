@@ -9,6 +9,8 @@
 #include "../../include/slabhash.h"
 #include "slab_device.cuh"
 
+struct slab_host_io;  // staging of batches from host memory (host_batch.cu)
+
 struct slab_table {
     int device = 0;
     int sm_count = 0;
@@ -34,9 +36,13 @@ struct slab_table {
     bool owns_memory = true;          // false for a table that lives inside a slab_group's arena
     bool multiset = false;            // duplicates allowed (INSERT), deletes empty their slot
     int occupancy[2][4] = {};         // resident blocks per SM by [variant][kernel kind] for cfg; 0 = not yet asked
+    slab_host_io* host_io = nullptr;  // device staging of slab_batch_host, made on its first call
 };
 
 namespace slab_host {
+
+// Frees the table's staging for batches from host memory (host_batch.cu).
+void free_host_io(slab_table* t);
 
 inline unsigned long long* counters(const slab_table* t) {
     return reinterpret_cast<unsigned long long*>(t->d_misc + 2);

@@ -447,6 +447,7 @@ int slab_create_seeded(uint32_t num_buckets, int mode, uint64_t seed, uint64_t p
 void slab_destroy(slab_table* t) {
     if (!t || !t->owns_memory) return;  // tables of a group are freed with the group
     cudaDeviceSynchronize();
+    slab_host::free_host_io(t);
     cudaFree(t->d_slabs);
     cudaFree(t->d_bitmaps);
     cudaFree(t->d_misc);

@@ -38,7 +38,7 @@ EXPORTED = [
     "slab_server_get_stats", "slab_server_run",
     "slab_set_multiset", "slab_search_all_batch", "slab_delete_all_batch", "slab_flush", "slab_grow_pool",
     "slab_hash_params", "slab_create_seeded", "slab_probe_random_or", "slab_probe_random_lines_v4",
-    "slab_create_width", "slab_group_create_width",
+    "slab_create_width", "slab_group_create_width", "slab_batch_host",
 ]
 SLAB_SERVER_MAX_SLOTS, SLAB_SERVER_MAX_REQUEST_OPS, SLAB_SERVER_ZERO_COPY, SLAB_SERVER_GROW_POOL = 64, 1 << 24, 1, 2
 SLAB_LEARN_AUTO, SLAB_LEARN_ALWAYS, SLAB_LEARN_MEASURE = 0, 1, 2
@@ -117,6 +117,7 @@ def load_library(build_if_stale: bool = True) -> C.CDLL:
             "slab_probe_random_lines": (i32, [vp, u64, u64, u32, i32, i32, vp, vp]),
             "slab_probe_random_lines_v4": (i32, [vp, u64, u64, u32, i32, i32, i32, i32, vp, vp]),
             "slab_create_width": (i32, [u32, i32, u32, u32, u32, u64, C.POINTER(vp)]),
+            "slab_batch_host": (i32, [vp, i32, vp, vp, vp, vp, vp, u32, u32, vp, vp]),
             "slab_group_create_width": (i32, [u32, vp, vp, vp, vp, i32, u32, C.POINTER(vp)]),
             "slab_probe_random_cas": (i32, [vp, u64, u64, u32, i32, i32, vp]),
             "slab_chain_histogram_noalloc": (i32, [vp, u32, C.POINTER(u64), C.POINTER(u64), vp]),
@@ -194,6 +195,43 @@ def slab_create_width(num_buckets: int, mode: int, slab_bytes: int, hash_a: int,
     _check(load_library().slab_create_width(num_buckets, mode, slab_bytes, hash_a, hash_b, pool_slabs, C.byref(h)),
            "slab_create_width")
     return h.value
+
+
+SLAB_BATCH_INSERT, SLAB_BATCH_DELETE, SLAB_BATCH_SEARCH, SLAB_BATCH_MIXED = 0, 1, 2, 3
+
+
+def _host_ptr(a, itemsize: int, n: int, name: str, nullable: bool = False):
+    """Host address of a contiguous numpy array or CPU torch tensor with n elements of itemsize bytes."""
+    if a is None:
+        if nullable:
+            return None
+        raise ValueError(f"{name} is required")
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous() or a.element_size() != itemsize or a.numel() < n:
+            raise ValueError(f"{name}: a contiguous host tensor of {n} x {itemsize}-byte elements is required")
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"] or a.itemsize != itemsize or a.size < n:
+        raise ValueError(f"{name}: a contiguous host array of {n} x {itemsize}-byte elements is required")
+    return a.ctypes.data
+
+
+def slab_batch_host(t: int, kind: int, keys, values=None, ops=None, results=None, found=None, n: int | None = None,
+                    chunk: int = 0, stream=None, done_event=None) -> None:
+    """A batch from host memory (slabhash.h slab_batch_host); done_event: a torch.cuda.Event or None."""
+    n = (keys.numel() if isinstance(keys, torch.Tensor) else len(keys)) if n is None else n
+    ev = None
+    if done_event is not None:
+        if hasattr(done_event, "cuda_event"):  # a torch.cuda.Event: its CUDA event exists once it is recorded
+            if not done_event.cuda_event:
+                done_event.record()
+            ev = done_event.cuda_event
+        else:
+            ev = done_event
+    _check(load_library().slab_batch_host(
+        t, int(kind), _host_ptr(ops, 1, n, "ops", nullable=True), _host_ptr(keys, 4, n, "keys"),
+        _host_ptr(values, 4, n, "values", nullable=True), _host_ptr(results, 4, n, "results", nullable=True),
+        _host_ptr(found, 1, n, "found", nullable=True), n, int(chunk), _stream(stream), ev), "slab_batch_host")
 
 
 def slab_create(num_buckets: int, mode: int, hash_a: int, hash_b: int, pool_slabs: int) -> int:
