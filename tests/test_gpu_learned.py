@@ -16,8 +16,8 @@ def _lib():
     sh.load_library()
 
 
-def _fit_both(keys, B, stride, policy=sh.SLAB_LEARN_ALWAYS, variant="staged", a=5, b=7):
-    p = Pair(B, a, b, variant=variant, n_hint=len(keys))
+def _fit_both(keys, B, stride, policy=sh.SLAB_LEARN_ALWAYS, variant="staged", a=5, b=7, slab_bytes=128):
+    p = Pair(B, a, b, variant=variant, n_hint=len(keys), slab_bytes=slab_bytes)
     rep = sh.slab_learn_buckets(p.g.handle, dev(keys), stride, policy)
     model_g, in_use = sh.slab_get_model(p.g.handle)
     model_o, m = learn_model(keys, stride, B)
@@ -56,6 +56,25 @@ def test_learned_table_parity(variant):
         live = np.setdiff1d(w.keys, w.keys[::5])
         mb, _ = W.mixed_batch(W.KeyStream(99), live, 1 << 13, (0.2, 0.2, 0.6), rng)
         p.mixed(mb.ops, mb.keys, mb.values)
+        p.check_structure()
+    finally:
+        p.close()
+
+
+def test_learned_table_parity_at_64_bytes():
+    """The learned bucket function on a table of 64-byte slabs: the GPU fit equals the
+    oracle's, and every op and the table structure agree with an oracle of 7 pairs
+    per slab on that model."""
+    w = W.config4(seed=5, n=1 << 16, beta=0.6)
+    B = W.buckets_for(len(w.keys), 0.6, 7)
+    p, rep, model_g, _, model_o, _ = _fit_both(w.keys, B, 100, slab_bytes=64)
+    try:
+        assert model_g.view(np.uint32).tolist() == model_o.view(np.uint32).tolist()
+        p.o.use_model(model_o)
+        p.insert(w.keys, w.values)
+        _, found = p.search(w.search.keys)
+        assert (found.astype(bool) == w.search.present).all()
+        p.delete(w.keys[::3])
         p.check_structure()
     finally:
         p.close()
