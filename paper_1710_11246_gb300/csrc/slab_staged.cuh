@@ -45,11 +45,14 @@ constexpr uint32_t kNoOpCode = 0xFFu;
 template <uint32_t kW>
 constexpr uint32_t kServeWordsPerWarp = kTileWords<kW> + 32u + 32u + 32u;
 // Search and delete kernels add the ring of deferred ops behind that: op index,
-// slab to stage next, key and rounds so far, kDeferSlots of each. The largest
-// per-warp layout of the staged kernels is kStagedWordsPerWarp.
+// slab to stage next, key and rounds so far, kDeferSlots of each. Mixed kernels
+// keep each ring entry's op code too, and a queue of inserts (op index, key,
+// value, bucket); theirs is the largest per-warp layout, kMixedWordsPerWarp.
 constexpr uint32_t kDeferSlots = 64u;
 template <uint32_t kW>
 constexpr uint32_t kStagedWordsPerWarp = kServeWordsPerWarp<kW> + 4u * kDeferSlots;
+template <uint32_t kW>
+constexpr uint32_t kMixedWordsPerWarp = kServeWordsPerWarp<kW> + 9u * kDeferSlots;
 
 // The second value a mixed op's WCWS step matches besides its key: an empty
 // slot for an insert (it may claim one), its key again for a search or delete.
@@ -234,20 +237,23 @@ __device__ __forceinline__ uint32_t own_ballot(const uint32_t* ballots, uint32_t
 // every source lane acts on its ballot (reads the value, or writes the tombstone). On return
 // an op that is done has its result in res / fnd and pending cleared; one that
 // goes on has u set to its list's next slab.
+// (kKind = kKindMixed: each lane's op is a search or a delete, given by `op`.)
 template <int kKind, bool kKeyOnly, uint32_t kW>
 __device__ __forceinline__ void read_round(const TableView& T, const uint32_t* buf, uint32_t* ballots,
                                            const uint32_t* skeys, const uint32_t (&off)[8], uint32_t pend,
-                                           bool& pending, uint32_t& u, uint32_t& res, uint32_t& fnd) {
-    static_assert(kKind == kKindSearch || kKind == kKindDelete, "claims serve whole tiles (serve_tile)");
+                                           bool& pending, uint32_t& u, uint32_t& res, uint32_t& fnd,
+                                           uint32_t op = kOpSearch) {
+    static_assert(kKind != kKindInsert, "claims serve whole tiles (serve_tile)");
     const uint32_t lane = lane_id();
-    wcws_ballots<kKind, kW>(buf, ballots, skeys, skeys, off, pend, pend == kFull, __popc(pend) > 8);
+    // a search or delete step compares the op's key only
+    wcws_ballots<kKindSearch, kW>(buf, ballots, skeys, skeys, off, pend, pend == kFull, __popc(pend) > 8);
     __syncwarp();
     // the source lanes act on their ballots (Sec. 4.3)
     const uint32_t m = pending ? own_ballot<kKeyOnly, kW>(ballots, lane) : 0u;
     if (pending) {
         if (m) {
             const uint32_t d = (uint32_t)(__ffs(m) - 1);
-            if constexpr (kKind == kKindSearch) {
+            if (kKind == kKindSearch || (kKind == kKindMixed && op == kOpSearch)) {
                 res = kKeyOnly ? 0u : buf[swz<kW>(lane, d + 1u)];
             } else {
                 remove_at<kKeyOnly>(T, T.slabs + (uint64_t)u * kW, d);
@@ -444,7 +450,8 @@ template <int kKind>
 constexpr bool kClaims = kKind == kKindInsert || kKind == kKindMixed;
 // shared memory words per warp of a kind's kernel (the ring only where ops wait in one)
 template <int kKind, uint32_t kW>
-constexpr uint32_t kWordsPerWarp = kClaims<kKind> ? kServeWordsPerWarp<kW> : kStagedWordsPerWarp<kW>;
+constexpr uint32_t kWordsPerWarp = kKind == kKindInsert ? kServeWordsPerWarp<kW>
+                                   : (kKind == kKindMixed ? kMixedWordsPerWarp<kW> : kStagedWordsPerWarp<kW>);
 
 // kW: words per slab, 32 (128-byte slabs) or 16 (64-byte slabs)
 template <int kKind, bool kKeyOnly, uint32_t kW>
@@ -463,6 +470,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
     uint32_t* q_u = q_idx + kDeferSlots;
     uint32_t* q_key = q_u + kDeferSlots;
     uint32_t* q_rounds = q_key + kDeferSlots;
+    uint32_t* q_op = q_rounds + kDeferSlots;  // mixed kernels: the ring's op codes, then the insert queue
     const uint32_t buf_s = (uint32_t)__cvta_generic_to_shared(buf);
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -497,7 +505,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
     // Search / delete ops that must go on to another slab wait in a ring of
     // kDeferSlots entries; qh / qn: its head and count (warp-uniform).
     uint32_t qh = 0u, qn = 0u;
-    auto push = [&](bool keep, uint32_t i, uint32_t uu, uint32_t k, uint32_t r) {
+    auto push = [&](bool keep, uint32_t i, uint32_t uu, uint32_t k, uint32_t r, uint32_t op) {
         const uint32_t b = __ballot_sync(kFull, keep);
         if (keep) {
             const uint32_t pos = (qh + qn + __popc(b & ((1u << lane) - 1u))) & (kDeferSlots - 1u);
@@ -505,6 +513,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
             q_u[pos] = uu;
             q_key[pos] = k;
             q_rounds[pos] = r;
+            if constexpr (kKind == kKindMixed) q_op[pos] = op;
         }
         qn += __popc(b);
         __syncwarp();
@@ -515,6 +524,109 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
             pending = false;
         }
     };
+    // tiles of waiting ops: whenever 32 wait, and (last) after the warp's last
+    // tile until the ring is empty
+    auto drain = [&](bool last) {
+        if constexpr (kKind != kKindInsert) {
+            while (qn >= 32u || (last && qn)) {
+                const uint32_t take = qn < 32u ? qn : 32u;
+                const bool mine = lane < take;
+                const uint32_t pos = (qh + lane) & (kDeferSlots - 1u);
+                uint32_t i = 0u, uu = 0u, k = 0u, rr = 0u, op = fixed_op<kKind == kKindMixed ? kKindSearch : kKind>();
+                if (mine) {
+                    i = q_idx[pos];
+                    uu = q_u[pos];
+                    k = q_key[pos];
+                    rr = q_rounds[pos];
+                    if constexpr (kKind == kKindMixed) op = q_op[pos];
+                }
+                qh = (qh + take) & (kDeferSlots - 1u);
+                qn -= take;
+                const uint32_t pm = take >= 32u ? kFull : (1u << take) - 1u;
+                stage_slabs<kW>(T, buf_s, uu, pm, lane);
+                cp_async_commit();
+                skeys[lane] = match_key(T, k, op);
+                cp_async_wait<0>();
+                __syncwarp();
+                bool more = mine;
+                uint32_t rs = default_result(op), fd = 0u;
+                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pm, more, uu, rs, fd, op);
+                round_done(more, rr);
+                if (mine && !more) {
+                    if (A.results) A.results[i] = rs;
+                    if (A.found) A.found[i] = (uint8_t)fd;
+                }
+                __syncwarp();
+                push(more, i, uu, k, rr, op);
+            }
+        }
+    };
+
+    if constexpr (kKind == kKindMixed) {
+        if (!T.prefetch_l2) {
+            // Mixed batches on L2-resident tables: each input tile's ops are sorted by
+            // kind into two per-warp queues, inserts (served as tiles of the insert
+            // kernel's claim rounds) and searches / deletes (the ring, served with
+            // read rounds), so that every tile the warp serves holds one kind of op.
+            uint32_t* i_idx = q_op + kDeferSlots;
+            uint32_t* i_key = i_idx + kDeferSlots;
+            uint32_t* i_val = i_key + kDeferSlots;
+            uint32_t* i_bkt = i_val + kDeferSlots;
+            uint32_t ih = 0u, in = 0u;  // the insert queue's head and count (warp-uniform)
+            uint32_t ck, cv, co;
+            fetch(t, ck, cv, co);
+            for (; t < ntiles; t += nwarps) {
+                uint32_t nk, nv, no;
+                fetch(t + nwarps, nk, nv, no);
+                const uint32_t idx = t * 32u + lane;
+                if (co <= kOpSearch && ck >= kTombstone) set_flag(T, kFlagReserved);
+                const bool walk = walks(ck, co);
+                if (idx < A.n && !walk) {  // reserved keys and unknown op codes
+                    if (A.results) A.results[idx] = default_result(co);
+                    if (A.found) A.found[idx] = 0u;
+                }
+                const uint32_t b = walk ? bucket_of(T, ck) : 0u;
+                const bool ins = walk && co == kOpInsert;
+                const uint32_t im = __ballot_sync(kFull, ins);
+                if (ins) {
+                    const uint32_t pos = (ih + in + __popc(im & ((1u << lane) - 1u))) & (kDeferSlots - 1u);
+                    i_idx[pos] = idx;
+                    i_key[pos] = ck;
+                    i_val[pos] = cv;
+                    i_bkt[pos] = b;
+                }
+                in += __popc(im);
+                push(walk && !ins, idx, b, ck, 0u, co);
+                const bool last = t + nwarps >= ntiles;
+                while (in >= 32u || (last && in)) {
+                    const uint32_t take = in < 32u ? in : 32u;
+                    const bool mine = lane < take;
+                    const uint32_t pos = (ih + lane) & (kDeferSlots - 1u);
+                    uint32_t i = 0u, k = 0u, v = 0u, bk = 0u, o = kNoOpCode;
+                    if (mine) {
+                        i = i_idx[pos];
+                        k = i_key[pos];
+                        v = i_val[pos];
+                        bk = i_bkt[pos];
+                        o = kOpInsert;
+                    }
+                    ih = (ih + take) & (kDeferSlots - 1u);
+                    in -= take;
+                    stage_slabs<kW>(T, buf_s, bk, take >= 32u ? kFull : (1u << take) - 1u, lane);
+                    cp_async_commit();
+                    skeys[lane] = match_key(T, k, o);
+                    cp_async_wait<0>();
+                    __syncwarp();
+                    serve_tile<kKindInsert, kKeyOnly, kW>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, k,
+                                                          v, o, bk, i, mine);
+                    __syncwarp();
+                }
+                drain(last);
+                ck = nk; cv = nv; co = no;
+            }
+            return;
+        }
+    }
 
     // prologue: this tile hashed (its base slabs pulled into L2 for big tables),
     // the next tile loading
@@ -563,40 +675,8 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
                 if (A.found) A.found[idx] = (uint8_t)fnd;
             }
             __syncwarp();
-            push(pending, idx, u, ck, r);
-            // tiles of waiting ops: whenever 32 wait, and after the warp's last
-            // tile until the ring is empty
-            const bool last = t + nwarps >= ntiles;
-            while (qn >= 32u || (last && qn)) {
-                const uint32_t take = qn < 32u ? qn : 32u;
-                const bool mine = lane < take;
-                const uint32_t pos = (qh + lane) & (kDeferSlots - 1u);
-                uint32_t i = 0u, uu = 0u, k = 0u, rr = 0u;
-                if (mine) {
-                    i = q_idx[pos];
-                    uu = q_u[pos];
-                    k = q_key[pos];
-                    rr = q_rounds[pos];
-                }
-                qh = (qh + take) & (kDeferSlots - 1u);
-                qn -= take;
-                const uint32_t pm = take >= 32u ? kFull : (1u << take) - 1u;
-                stage_slabs<kW>(T, buf_s, uu, pm, lane);
-                cp_async_commit();
-                skeys[lane] = match_key(T, k, fixed_op<kKind>());
-                cp_async_wait<0>();
-                __syncwarp();
-                bool more = mine;
-                uint32_t rs = default_result(fixed_op<kKind>()), fd = 0u;
-                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pm, more, uu, rs, fd);
-                round_done(more, rr);
-                if (mine && !more) {
-                    if (A.results) A.results[i] = rs;
-                    if (A.found) A.found[i] = (uint8_t)fd;
-                }
-                __syncwarp();
-                push(more, i, uu, k, rr);
-            }
+            push(pending, idx, u, ck, r, fixed_op<kKind>());
+            drain(t + nwarps >= ntiles);
         }
         // (4) rotate the pipeline
         ck = nk; cv = nv; co = no; cb = nb;

@@ -52,9 +52,9 @@ bool valid_config(const slab_config& c) {
     return (c.variant == SLAB_VARIANT_STAGED || c.variant == SLAB_VARIANT_DIRECT) &&
            c.threads_per_block >= 32 && c.threads_per_block <= 1024 && c.threads_per_block % 32 == 0 &&
            c.blocks_per_sm >= 0 && c.blocks_per_sm <= 64 && c.iter_limit >= 1 && c.random_probes <= (1u << 20) &&
-           // staged kernels hold one 4 KB stage per warp, plus up to 1.4 KB of keys, ballots and waiting ops
+           // staged kernels hold one 4 KB stage per warp, plus up to 2.7 KB of keys, ballots and waiting ops
            (c.variant != SLAB_VARIANT_STAGED ||
-            c.threads_per_block / 32 * kStagedWordsPerWarp<32u> * 4 <= 227 * 1024);
+            c.threads_per_block / 32 * kMixedWordsPerWarp<32u> * 4 <= 227 * 1024);
 }
 
 // The largest block every staged kernel of a mode and slab width can launch:

@@ -162,6 +162,54 @@ def test_mixed_batches(variant):
         p.close()
 
 
+def _kind_runs(kind, n, rng):
+    """Op codes for n ops: one kind only, alternating, or in long runs of one kind
+    (the first third inserts, then deletes, then searches), with unknown codes
+    sprinkled in where `kind` says so."""
+    if kind in (0, 1, 2):
+        return np.full(n, kind, np.uint8)
+    if kind == "alternate":
+        return (np.arange(n) % 3).astype(np.uint8)
+    if kind == "runs":
+        return np.minimum(np.arange(n) * 3 // max(n, 1), 2).astype(np.uint8)
+    ops = rng.integers(0, 3, n).astype(np.uint8)  # "unknown": a few codes past search
+    odd = rng.random(n) < 0.1
+    ops[odd] = rng.integers(3, 256, int(odd.sum())).astype(np.uint8)
+    return ops
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 100, 4097])
+@pytest.mark.parametrize("kind", [0, 1, 2, "alternate", "runs", "unknown"])
+@pytest.mark.parametrize("tpb", [128, 32])
+def test_mixed_batches_of_one_kind_and_ragged_sizes(n, kind, tpb):
+    """Staged mixed kernels sort each tile's ops into a queue of inserts and a ring
+    of searches and deletes, and serve each as tiles of their own: batches of one
+    kind only, of alternating kinds and of long runs of one kind, at ragged sizes
+    (so both queues end in partial tiles), with unknown op codes, and on the
+    smallest grid (each warp then serves many tiles and both queues wrap), agree
+    with the oracle. Keys are distinct within a batch."""
+    ks = W.KeyStream(1000 + n)
+    pre = ks.take(2 * n)
+    a, b = W.hash_params(n + 11)
+    rng = np.random.default_rng(n)
+    for B in (1, 3, max(1, n // 9)):
+        p = Pair(B, a, b, n_hint=4 * n, threads_per_block=tpb, blocks_per_sm=1 if tpb == 32 else 0)
+        try:
+            p.insert(pre, W.values_for(pre))
+            ops = _kind_runs(kind, n, rng)
+            # inserts take fresh keys; deletes and searches take preloaded keys
+            # (half of the searches miss)
+            fresh = ks.take(n)
+            keys = np.where(ops == 0, fresh, pre[rng.permutation(2 * n)[:n]]).astype(np.uint32)
+            miss = (ops == 2) & (rng.random(n) < 0.5)
+            keys[miss] = ks.take(int(miss.sum()))
+            p.mixed(ops, keys, W.values_for(keys))
+            p.search(np.concatenate([pre, fresh]))
+            p.check_structure()
+        finally:
+            p.close()
+
+
 @pytest.mark.parametrize("variant", list(VARIANTS))
 def test_pool_exhaustion_reports_and_stays_consistent(variant):
     """One memory block (1024 slabs) cannot hold 2^15 pairs in one bucket: some inserts
@@ -512,9 +560,10 @@ def test_growth_burst_in_a_tight_pool(variant):
 
 @pytest.mark.parametrize("variant,key_only", [("staged", False), ("staged", True), ("direct", False)])
 def test_long_lists_in_a_table_larger_than_l2(variant, key_only):
-    """Search and delete on a table whose base slabs (2^20 x 128 B = 134 MB) are far
-    larger than half the L2, the case where those kernels restage an op's next slab
-    inside its tile (and pull slabs into L2 ahead) instead of parking the op. With
+    """Search, delete and mixed batches on a table whose base slabs (2^20 x 128 B =
+    134 MB) are far larger than half the L2, the case where those kernels restage
+    an op's next slab inside its tile (and pull slabs into L2 ahead) instead of
+    parking the op. With
     h(k) = k mod B (a = 1, b = 0) the keys bucket + j * B fill 1000 lists with 60
     keys each (4 slabs in key-value mode, 2 in key-only mode); hits, misses and
     deletes along the lists agree with the oracle. The one batch of inserts also
@@ -535,6 +584,18 @@ def test_long_lists_in_a_table_larger_than_l2(variant, key_only):
         p.search(np.concatenate([stored, absent[::5]]))
         tot = p.check_structure()
         assert tot["slabs"] == B + (1000 if key_only else 3000)
+        if variant == "staged":
+            # one mixed batch along the same lists: deletes and hits of stored keys,
+            # misses and inserts of absent ones (the inserts grow some lists again)
+            live = np.setdiff1d(stored, stored[::3])
+            ins, miss = absent[1::5][:4000], absent[2::5]
+            keys = np.concatenate([ins, live[:6000], live[6000:20000], miss]).astype(np.uint32)
+            ops = np.concatenate([np.zeros(len(ins), np.uint8), np.ones(6000, np.uint8),
+                                  np.full(len(keys) - len(ins) - 6000, 2, np.uint8)])
+            perm = rng.permutation(len(keys))
+            p.mixed(ops[perm], keys[perm], W.values_for(keys[perm]))
+            p.search(np.concatenate([live, ins]))
+            p.check_structure()
     finally:
         p.close()
 
