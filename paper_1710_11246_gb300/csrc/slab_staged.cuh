@@ -231,6 +231,39 @@ __device__ __forceinline__ uint32_t own_ballot(const uint32_t* ballots, uint32_t
     else return (ballots[lane >> 1] >> ((lane & 1u) * 16u)) & key_words<kKeyOnly, 16u>();
 }
 
+// The staged kernels match with the source lane scanning its own op's staged slab
+// (SLAB_LANE_MATCH = 1) or with the WCWS ballots above (0). The stage already came
+// in as coalesced, warp-cooperative copies of whole slabs, so the per-op compares
+// need no warp-wide step: a lane reads its slot as 16-byte chunks (8 lanes of a
+// quarter-warp hit 8 distinct chunk positions under the stage's swizzle).
+#ifndef SLAB_LANE_MATCH
+#define SLAB_LANE_MATCH 1
+#endif
+
+// The lowest key word of slot `lane` that holds `key` or (kAlt) `alt`, as the one
+// bit of the mask own_ballot would give it (0: no match).
+template <bool kKeyOnly, uint32_t kW, bool kAlt>
+__device__ __forceinline__ uint32_t lane_match(const uint32_t* buf, uint32_t lane, uint32_t key, uint32_t alt) {
+    constexpr uint32_t kKeys = key_words<kKeyOnly, kW>();
+    uint32_t d = 32u;
+#pragma unroll
+    for (int c = (int)(kW / 4u) - 1; c >= 0; --c) {  // from the last chunk, so the lowest match stays
+        if ((kKeys >> (4 * c)) & 0xFu) {
+            const uint4 q = *reinterpret_cast<const uint4*>(buf + swz<kW>(lane, 4u * (uint32_t)c));
+            const uint32_t w[4] = {q.w, q.z, q.y, q.x};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {  // words 4c + 3 down to 4c
+                const uint32_t wi = 4u * (uint32_t)c + 3u - (uint32_t)j;
+                if ((kKeys >> wi) & 1u) {
+                    const bool hit = w[j] == key || (kAlt && w[j] == alt);
+                    d = hit ? wi : d;
+                }
+            }
+        }
+    }
+    return d < 32u ? 1u << d : 0u;
+}
+
 // One WCWS round (Fig. "alg:search") of a search or delete batch for the ops of
 // the lanes in `pend`, each of whose current slab (unified index u) is staged in
 // slot `lane` of `buf`, with keys in `skeys`: the ballots of wcws_ballots, then
@@ -242,14 +275,19 @@ template <int kKind, bool kKeyOnly, uint32_t kW>
 __device__ __forceinline__ void read_round(const TableView& T, const uint32_t* buf, uint32_t* ballots,
                                            const uint32_t* skeys, const uint32_t (&off)[8], uint32_t pend,
                                            bool& pending, uint32_t& u, uint32_t& res, uint32_t& fnd,
-                                           uint32_t op = kOpSearch) {
+                                           uint32_t key, uint32_t op = kOpSearch) {
     static_assert(kKind != kKindInsert, "claims serve whole tiles (serve_tile)");
     const uint32_t lane = lane_id();
-    // a search or delete step compares the op's key only
-    wcws_ballots<kKindSearch, kW>(buf, ballots, skeys, skeys, off, pend, pend == kFull, __popc(pend) > 8);
-    __syncwarp();
-    // the source lanes act on their ballots (Sec. 4.3)
-    const uint32_t m = pending ? own_ballot<kKeyOnly, kW>(ballots, lane) : 0u;
+    uint32_t m;
+    if constexpr (SLAB_LANE_MATCH) {
+        m = pending ? lane_match<kKeyOnly, kW, false>(buf, lane, key, key) : 0u;
+    } else {
+        // a search or delete step compares the op's key only
+        wcws_ballots<kKindSearch, kW>(buf, ballots, skeys, skeys, off, pend, pend == kFull, __popc(pend) > 8);
+        __syncwarp();
+        // the source lanes act on their ballots (Sec. 4.3)
+        m = pending ? own_ballot<kKeyOnly, kW>(ballots, lane) : 0u;
+    }
     if (pending) {
         if (m) {
             const uint32_t d = (uint32_t)(__ffs(m) - 1);
@@ -302,12 +340,24 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
             cp_async_wait<0>();
             __syncwarp();
         }
-        // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
-        wcws_ballots<kKind, kW>(buf, ballots, skeys, salts, off, pend, first && pend == kFull, first);
-        __syncwarp();
-
-        // the source lanes act on their ballots (Sec. 4.3)
-        const uint32_t m = pending ? own_ballot<kKeyOnly, kW>(ballots, lane) : 0u;
+        uint32_t m;
+        if constexpr (SLAB_LANE_MATCH) {
+            // each pending op's lane scans its slab for its key (and an insert for
+            // EMPTY, a mixed op for its alternate key)
+            const uint32_t sk = match_key(T, ck, co);
+            if constexpr (kKind == kKindInsert || kKind == kKindMixed)
+                m = pending ? lane_match<kKeyOnly, kW, true>(buf, lane, sk, kKind == kKindMixed ? alt_key(ck, co)
+                                                                                                 : kEmptyKey)
+                            : 0u;
+            else
+                m = pending ? lane_match<kKeyOnly, kW, false>(buf, lane, sk, sk) : 0u;
+        } else {
+            // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
+            wcws_ballots<kKind, kW>(buf, ballots, skeys, salts, off, pend, first && pend == kFull, first);
+            __syncwarp();
+            // the source lanes act on their ballots (Sec. 4.3)
+            m = pending ? own_ballot<kKeyOnly, kW>(ballots, lane) : 0u;
+        }
         uint32_t* gslab = T.slabs + (uint64_t)u * kW;
         const uint32_t myop = kKind == kKindMixed ? co : fixed_op<kKind>();
         bool cas_wait = false, cas_new = false, need_slab = false;
@@ -550,7 +600,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
                 __syncwarp();
                 bool more = mine;
                 uint32_t rs = default_result(op), fd = 0u;
-                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pm, more, uu, rs, fd, op);
+                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pm, more, uu, rs, fd, k, op);
                 round_done(more, rr);
                 if (mine && !more) {
                     if (A.results) A.results[i] = rs;
@@ -667,7 +717,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
             const uint32_t pend = __ballot_sync(kFull, pending);
             uint32_t res = default_result(co), fnd = 0u, u = cb, r = 0u;
             if (pend) {
-                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pend, pending, u, res, fnd);
+                read_round<kKind, kKeyOnly, kW>(T, buf, ballots, skeys, off, pend, pending, u, res, fnd, ck);
                 round_done(pending, r);
             }
             if (idx < A.n && !pending) {
