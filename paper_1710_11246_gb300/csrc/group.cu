@@ -164,8 +164,10 @@ __global__ void __maxnreg__(SLAB_GROUP_MAXNREG)
         //     publish this tile's keys
         const uint32_t nb = bucket(n);
         const Tile m = fetch(g + 2u * nwarps);
-        skeys[lane] = match_key(T, c.k, c.o);
-        if constexpr (kKind == kKindMixed) salts[lane] = alt_key(c.k, c.o);
+        if constexpr (!SLAB_LANE_MATCH) {  // the WCWS steps read the tile's keys from here
+            skeys[lane] = match_key(T, c.k, c.o);
+            if constexpr (kKind == kKindMixed) salts[lane] = alt_key(c.k, c.o);
+        }
         // (3) serve this tile once its slabs have landed
         cp_async_wait<0>();
         __syncwarp();

@@ -240,16 +240,35 @@ __device__ __forceinline__ uint32_t own_ballot(const uint32_t* ballots, uint32_t
 #define SLAB_LANE_MATCH 1
 #endif
 
+#ifndef SLAB_LANE_VALUE
+#define SLAB_LANE_VALUE 1
+#endif
+
+// One 16-byte chunk of the stage as a single 128-bit shared load. Written out so
+// the load stays whole when only some of its words are used: split into 32-bit
+// loads, lanes s, s + 8, s + 16 and s + 24 (one chunk position under the swizzle)
+// would share banks, four ways. Volatile keeps it after the stage's cp.async wait.
+__device__ __forceinline__ uint4 ld_stage_chunk(const uint32_t* p) {
+    uint4 r;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+    return r;
+}
+
 // The lowest key word of slot `lane` that holds `key` or (kAlt) `alt`, as the one
-// bit of the mask own_ballot would give it (0: no match).
-template <bool kKeyOnly, uint32_t kW, bool kAlt>
-__device__ __forceinline__ uint32_t lane_match(const uint32_t* buf, uint32_t lane, uint32_t key, uint32_t alt) {
+// bit of the mask own_ballot would give it (0: no match). kVal (key-value slabs):
+// *val gets the word after that key, its value, from the same 16-byte chunk.
+template <bool kKeyOnly, uint32_t kW, bool kAlt, bool kVal = false>
+__device__ __forceinline__ uint32_t lane_match(const uint32_t* buf, uint32_t lane, uint32_t key, uint32_t alt,
+                                               uint32_t* val = nullptr) {
+    static_assert(!(kVal && kKeyOnly), "key-only slabs hold no values");
     constexpr uint32_t kKeys = key_words<kKeyOnly, kW>();
-    uint32_t d = 32u;
+    uint32_t d = 32u, v = 0u;
 #pragma unroll
     for (int c = (int)(kW / 4u) - 1; c >= 0; --c) {  // from the last chunk, so the lowest match stays
         if ((kKeys >> (4 * c)) & 0xFu) {
-            const uint4 q = *reinterpret_cast<const uint4*>(buf + swz<kW>(lane, 4u * (uint32_t)c));
+            const uint4 q = ld_stage_chunk(buf + swz<kW>(lane, 4u * (uint32_t)c));
             const uint32_t w[4] = {q.w, q.z, q.y, q.x};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {  // words 4c + 3 down to 4c
@@ -257,10 +276,12 @@ __device__ __forceinline__ uint32_t lane_match(const uint32_t* buf, uint32_t lan
                 if ((kKeys >> wi) & 1u) {
                     const bool hit = w[j] == key || (kAlt && w[j] == alt);
                     d = hit ? wi : d;
+                    if constexpr (kVal) v = hit ? w[j > 0 ? j - 1 : 0] : v;  // key words are even: j is 1 or 3
                 }
             }
         }
     }
+    if constexpr (kVal) *val = v;
     return d < 32u ? 1u << d : 0u;
 }
 
@@ -278,8 +299,12 @@ __device__ __forceinline__ void read_round(const TableView& T, const uint32_t* b
                                            uint32_t key, uint32_t op = kOpSearch) {
     static_assert(kKind != kKindInsert, "claims serve whole tiles (serve_tile)");
     const uint32_t lane = lane_id();
-    uint32_t m;
-    if constexpr (SLAB_LANE_MATCH) {
+    uint32_t m, val = 0u;
+    // search values come with the match (the value sits in its key's chunk)
+    constexpr bool kVal = SLAB_LANE_MATCH && SLAB_LANE_VALUE && !kKeyOnly && kKind != kKindDelete;
+    if constexpr (kVal) {
+        m = pending ? lane_match<kKeyOnly, kW, false, true>(buf, lane, key, key, &val) : 0u;
+    } else if constexpr (SLAB_LANE_MATCH) {
         m = pending ? lane_match<kKeyOnly, kW, false>(buf, lane, key, key) : 0u;
     } else {
         // a search or delete step compares the op's key only
@@ -292,7 +317,8 @@ __device__ __forceinline__ void read_round(const TableView& T, const uint32_t* b
         if (m) {
             const uint32_t d = (uint32_t)(__ffs(m) - 1);
             if (kKind == kKindSearch || (kKind == kKindMixed && op == kOpSearch)) {
-                res = kKeyOnly ? 0u : buf[swz<kW>(lane, d + 1u)];
+                if constexpr (kVal) res = val;
+                else res = kKeyOnly ? 0u : buf[swz<kW>(lane, d + 1u)];
             } else {
                 remove_at<kKeyOnly>(T, T.slabs + (uint64_t)u * kW, d);
                 res = 1u;
@@ -595,7 +621,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
                 const uint32_t pm = take >= 32u ? kFull : (1u << take) - 1u;
                 stage_slabs<kW>(T, buf_s, uu, pm, lane);
                 cp_async_commit();
-                skeys[lane] = match_key(T, k, op);
+                if constexpr (!SLAB_LANE_MATCH) skeys[lane] = match_key(T, k, op);
                 cp_async_wait<0>();
                 __syncwarp();
                 bool more = mine;
@@ -664,7 +690,7 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
                     in -= take;
                     stage_slabs<kW>(T, buf_s, bk, take >= 32u ? kFull : (1u << take) - 1u, lane);
                     cp_async_commit();
-                    skeys[lane] = match_key(T, k, o);
+                    if constexpr (!SLAB_LANE_MATCH) skeys[lane] = match_key(T, k, o);
                     cp_async_wait<0>();
                     __syncwarp();
                     serve_tile<kKindInsert, kKeyOnly, kW>(T, A, ac, warp_gid, buf, buf_s, ballots, skeys, salts, off, k,
@@ -698,8 +724,10 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
         if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kW);
         uint32_t mk, mv, mo;
         fetch(t + 2u * nwarps, mk, mv, mo);
-        skeys[lane] = match_key(T, ck, co);  // the WCWS steps read keys four at a time from here
-        if constexpr (kKind == kKindMixed) salts[lane] = alt_key(ck, co);
+        if constexpr (!SLAB_LANE_MATCH) {  // the WCWS steps read keys four at a time from here
+            skeys[lane] = match_key(T, ck, co);
+            if constexpr (kKind == kKindMixed) salts[lane] = alt_key(ck, co);
+        }
         // (3) serve this tile once its slabs have landed
         cp_async_wait<0>();
         __syncwarp();
