@@ -247,10 +247,11 @@ __device__ __forceinline__ uint32_t own_ballot(const uint32_t* ballots, uint32_t
 // One 16-byte chunk of the stage as a single 128-bit shared load. Written out so
 // the load stays whole when only some of its words are used: split into 32-bit
 // loads, lanes s, s + 8, s + 16 and s + 24 (one chunk position under the swizzle)
-// would share banks, four ways. Volatile keeps it after the stage's cp.async wait.
+// would share banks, four ways; a volatile load is not narrowed to the words
+// used. The volatile asm also keeps it after the stage's cp.async wait.
 __device__ __forceinline__ uint4 ld_stage_chunk(const uint32_t* p) {
     uint4 r;
-    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+    asm volatile("ld.volatile.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
                  : "r"((uint32_t)__cvta_generic_to_shared(p)));
     return r;
@@ -259,12 +260,13 @@ __device__ __forceinline__ uint4 ld_stage_chunk(const uint32_t* p) {
 // The lowest key word of slot `lane` that holds `key` or (kAlt) `alt`, as the one
 // bit of the mask own_ballot would give it (0: no match). kVal (key-value slabs):
 // *val gets the word after that key, its value, from the same 16-byte chunk.
-template <bool kKeyOnly, uint32_t kW, bool kAlt, bool kVal = false>
+// kWord: *word gets the matched key word itself (the key, or what matched `alt`).
+template <bool kKeyOnly, uint32_t kW, bool kAlt, bool kVal = false, bool kWord = false>
 __device__ __forceinline__ uint32_t lane_match(const uint32_t* buf, uint32_t lane, uint32_t key, uint32_t alt,
-                                               uint32_t* val = nullptr) {
+                                               uint32_t* val = nullptr, uint32_t* word = nullptr) {
     static_assert(!(kVal && kKeyOnly), "key-only slabs hold no values");
     constexpr uint32_t kKeys = key_words<kKeyOnly, kW>();
-    uint32_t d = 32u, v = 0u;
+    uint32_t d = 32u, v = 0u, kw = 0u;
 #pragma unroll
     for (int c = (int)(kW / 4u) - 1; c >= 0; --c) {  // from the last chunk, so the lowest match stays
         if ((kKeys >> (4 * c)) & 0xFu) {
@@ -277,11 +279,13 @@ __device__ __forceinline__ uint32_t lane_match(const uint32_t* buf, uint32_t lan
                     const bool hit = w[j] == key || (kAlt && w[j] == alt);
                     d = hit ? wi : d;
                     if constexpr (kVal) v = hit ? w[j > 0 ? j - 1 : 0] : v;  // key words are even: j is 1 or 3
+                    if constexpr (kWord) kw = hit ? w[j] : kw;
                 }
             }
         }
     }
     if constexpr (kVal) *val = v;
+    if constexpr (kWord) *word = kw;
     return d < 32u ? 1u << d : 0u;
 }
 
@@ -366,17 +370,15 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
             cp_async_wait<0>();
             __syncwarp();
         }
-        uint32_t m;
+        uint32_t m, mw = 0u, mv = 0u;
         if constexpr (SLAB_LANE_MATCH) {
             // each pending op's lane scans its slab for its key (and an insert for
-            // EMPTY, a mixed op for its alternate key)
+            // EMPTY, a mixed op for its alternate key), keeping the matched pair
             const uint32_t sk = match_key(T, ck, co);
-            if constexpr (kKind == kKindInsert || kKind == kKindMixed)
-                m = pending ? lane_match<kKeyOnly, kW, true>(buf, lane, sk, kKind == kKindMixed ? alt_key(ck, co)
-                                                                                                 : kEmptyKey)
-                            : 0u;
-            else
-                m = pending ? lane_match<kKeyOnly, kW, false>(buf, lane, sk, sk) : 0u;
+            constexpr bool kClaim = kKind == kKindInsert || kKind == kKindMixed;
+            m = pending ? lane_match<kKeyOnly, kW, kClaim, !kKeyOnly, kClaim>(
+                              buf, lane, sk, kKind == kKindMixed ? alt_key(ck, co) : kEmptyKey, &mv, &mw)
+                        : 0u;
         } else {
             // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
             wcws_ballots<kKind, kW>(buf, ballots, skeys, salts, off, pend, first && pend == kFull, first);
@@ -393,7 +395,8 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
             if (m) {
                 d = (uint32_t)(__ffs(m) - 1);
                 if (myop == kOpSearch) {
-                    res = kKeyOnly ? 0u : buf[swz<kW>(lane, d + 1u)];
+                    if constexpr (SLAB_LANE_MATCH) res = kKeyOnly ? 0u : mv;
+                    else res = kKeyOnly ? 0u : buf[swz<kW>(lane, d + 1u)];
                     fnd = 1u;
                     pending = false;
                 } else if (myop == kOpDelete) {
@@ -402,7 +405,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                     fnd = 1u;
                     pending = false;
                 } else if constexpr (kKeyOnly) {
-                    if (!T.multiset && buf[swz<kW>(lane, d)] == ck) {  // already present
+                    if (!T.multiset && (SLAB_LANE_MATCH ? mw : buf[swz<kW>(lane, d)]) == ck) {  // already present
                         res = 0u;
                         fnd = 1u;
                         pending = false;
@@ -413,7 +416,9 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                         cas_new = true;
                     }
                 } else {
-                    const uint2 pr = *reinterpret_cast<const uint2*>(buf + swz<kW>(lane, d));
+                    uint2 pr;
+                    if constexpr (SLAB_LANE_MATCH) pr = make_uint2(mw, mv);  // the matched pair, from the scan
+                    else pr = *reinterpret_cast<const uint2*>(buf + swz<kW>(lane, d));
                     cas_exp = pack_pair(pr.x, pr.y);
                     cas_got = atomicCAS(reinterpret_cast<unsigned long long*>(gslab + d), cas_exp,
                                         pack_pair(ck, cv));
@@ -510,8 +515,10 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
 
 // Register caps of the staged kernels: more resident warps hide more of each
 // tile's staging latency (all kernels) and claim round trip (insert, mixed).
-// Mixed batches run their three op kinds' actions side by side and do better
-// with a few more registers than bulk inserts.
+// Mixed kernels hold the claim rounds of their insert tiles and the read rounds
+// of their search / delete tiles, and do better with more registers than bulk
+// inserts (below 72, the 8 chunk reads of a scan no longer stay in flight
+// together).
 #ifndef SLAB_READ_MAXNREG
 #define SLAB_READ_MAXNREG 72
 #endif
@@ -519,7 +526,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
 #define SLAB_CLAIM_MAXNREG 56
 #endif
 #ifndef SLAB_MIXED_MAXNREG
-#define SLAB_MIXED_MAXNREG 64
+#define SLAB_MIXED_MAXNREG 72
 #endif
 
 template <int kKind>
