@@ -380,7 +380,7 @@ __device__ __forceinline__ void serve_tile(const TableView& T, const BatchArgs& 
                               buf, lane, sk, kKind == kKindMixed ? alt_key(ck, co) : kEmptyKey, &mv, &mw)
                         : 0u;
         } else {
-            // WCWS: one queued op at a time, lane order (Fig. "alg:search" lines 3-10).
+            // WCWS: one queued op at a time, lane order (the work-queue loop of Fig. "alg:search").
             wcws_ballots<kKind, kW>(buf, ballots, skeys, salts, off, pend, first && pend == kFull, first);
             __syncwarp();
             // the source lanes act on their ballots (Sec. 4.3)
@@ -720,12 +720,21 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
     uint32_t nk, nv, no;
     fetch(t + nwarps, nk, nv, no);
 
+    // Search and delete batches: an op code is the kind's where the tile has an
+    // op and none past the end, recomputed where needed instead of carried along
+    // the pipeline (registers for the scan's chunk reads).
+    auto opat = [&](uint32_t tt) -> uint32_t {
+        return tt < ntiles && tt * 32u + lane < A.n ? fixed_op<kKind == kKindMixed ? kKindSearch : kKind>()
+                                                    : (uint32_t)kNoOpCode;
+    };
     for (; t < ntiles; t += nwarps) {
+        if constexpr (!kClaims<kKind>) co = opat(t);
         // (1) this tile's base slabs start moving into the stage
         stage_slabs<kW>(T, buf_s, cb, __ballot_sync(kFull, walks(ck, co)), lane);
         cp_async_commit();
         // (2) meanwhile: hash the next tile (pulling its slabs into L2 for big
         //     tables), start loading the tile after it, publish this tile's keys
+        if constexpr (!kClaims<kKind>) no = opat(t + nwarps);
         const bool nwalk = walks(nk, no);
         const uint32_t nb = nwalk ? bucket_of(T, nk) : 0u;
         if (T.prefetch_l2 && nwalk) prefetch_l2(T.slabs + (uint64_t)nb * kW);
