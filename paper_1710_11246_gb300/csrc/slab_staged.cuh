@@ -558,10 +558,11 @@ __global__ void __maxnreg__(kKind == kKindMixed ? SLAB_MIXED_MAXNREG
     const uint32_t warp_gid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t ntiles = (A.n + 31u) / 32u;
-    // Launched as a programmatic dependent: let the next batch's grid be
-    // scheduled as our blocks retire, and touch no memory before the previous
-    // kernel on the stream has completed.
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // Launched as a programmatic dependent: touch no memory before the previous
+    // kernel on the stream has completed (griddepcontrol.wait below). The next
+    // batch's grid is scheduled as our blocks exit; triggering it at our start
+    // instead (griddepcontrol.launch_dependents) parks its blocks on the SMs of
+    // our tail and measured slower.
     uint32_t t = warp_gid;
     if (t >= ntiles) return;  // warp-uniform
 
