@@ -45,7 +45,7 @@ PHASES = ("reset", "build", "search", "delete", "mixed")
 # sources they were taken from (the headers that define the staged kernels' device
 # code) and are dropped as soon as those sources change.
 KERNEL_SOURCES = ("slab_device.cuh", "slab_wcws.cuh", "slab_staged.cuh")
-NCU_TRAFFIC = {"sources_sha256": "f9cde67c07f71e8d", "build": 103.20e6}
+NCU_TRAFFIC = {"sources_sha256": "56bfeb35bee3747b", "build": 103.35e6}
 
 
 def ncu_traffic(phase: str):
@@ -243,7 +243,7 @@ def gpu_arm(args, rank, world, device):
     def step(evs, at=None):
         """One step. evs is None (no events), a list of 6 events around every
         phase, or (with `at` a phase index) 4 events: step start, before and after
-        phase `at`, step end."""
+        phase `at` (not recorded when `at` is -1), step end."""
         calls = (lambda: sh.slab_reset(h, stream),
                  lambda: sh.slab_insert_batch(h, k_build, v_build, None, stream=stream),
                  lambda: sh.slab_search_batch(h, k_search, o_search, f_search, stream=stream),
@@ -296,8 +296,10 @@ def gpu_arm(args, rank, world, device):
     dom = max(PHASES[1:], key=lambda p: statistics.fmean(per_phase[p]))
     at = PHASES.index(dom)
 
-    # timed pass: K steps, events only at the step bounds and around the dominant
-    # kernel (its launch durations feed the roofline)
+    # timed pass: K steps, events at the step bounds and, in every tenth step (and
+    # the last), around the dominant kernel (its launch durations feed the
+    # roofline). An event between two batch kernels keeps the second from being
+    # launched as the first one's blocks exit, so the other steps carry none.
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -307,11 +309,12 @@ def gpu_arm(args, rank, world, device):
         time.sleep(0.25)
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for _ in range(args.steps):
+            for i in range(args.steps):
                 flush.zero_()
                 evs = new_events(4)
-                step(evs, at)
-                timed.append(evs)
+                probe = i % 10 == 9 or i == args.steps - 1
+                step(evs, at if probe else -1)
+                timed.append((evs, probe))
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         time.sleep(0.25)
@@ -320,8 +323,8 @@ def gpu_arm(args, rank, world, device):
     rc, flags = t.status(stream)
     if rc != sh.SLAB_OK:
         raise RuntimeError(f"device status after timed steps: rc={rc} flags={flags}")
-    step_ms = [evs[0].elapsed_time(evs[3]) for evs in timed]
-    dom_ms = [evs[1].elapsed_time(evs[2]) for evs in timed]
+    step_ms = [evs[0].elapsed_time(evs[3]) for evs, _ in timed]
+    dom_ms = [evs[1].elapsed_time(evs[2]) for evs, probe in timed if probe]
     total_ms = slowest_rank_ms(sum(step_ms), world)
 
     # end to end through the C ABI from pinned host buffers
