@@ -3,22 +3,25 @@
 //
 // Each warp walks tiles of 32 ops (one per lane) in a persistent grid. Per tile:
 //   the tile's 32 base slabs are copied into the warp's shared-memory stage
-//   (cp.async, 16 bytes per lane, 4 slabs per warp instruction); while they are
-//   in flight the warp hashes the next tile's keys (pulling its base slabs into
-//   L2 for tables much larger than L2) and starts loading the tile after;
-//   then the tile is served from the stage.
-// Serving a tile is the WCWS loop of Fig. "alg:search": the warp takes the queued
-// ops in lane order; for each one it reads the op's slab coalesced (word `lane`
-// per lane, here from the stage), takes the op's key from the shared copy of the
-// tile's keys and finds matching or empty key lanes by ballot. The ballot word is
-// parked in shared memory and the source lane then acts on it: it reads the
-// value (search), writes the tombstone (delete) or issues the 64-bit CAS of the
-// pair (replace). All source lanes act in the same instructions, so the 32 CASes
-// of a tile are in flight together and their results are checked once. A claim
-// that lost its race tries the following pair of the same slab at once; ops that
-// must follow a next pointer, or that ran off their slab, restage just their
-// slabs and go round again; a full list grows through SlabAlloc (Sec. 5), by one
-// batched allocation for all of a bulk-insert tile's full lists.
+//   (cp.async, 16 bytes per lane, 4 slabs per warp instruction: the coalesced,
+//   warp-cooperative ReadSlab of Sec. 4.3 for 32 ops at once); while they are in
+//   flight the warp hashes the next tile's keys (pulling its base slabs into L2
+//   for tables much larger than L2) and starts loading the tile after; then the
+//   tile is served from the stage.
+// Serving a tile: each pending op's own lane scans its staged slab (8 128-bit
+// chunk reads) for the lowest key word that holds its key (an insert: its key or
+// an empty pair), the position the WCWS ballot of Fig. "alg:search" would give
+// the op's source lane. Built with -DSLAB_LANE_MATCH=0 the kernels run that WCWS
+// loop itself instead: the warp takes the queued ops in lane order, reads each
+// op's staged slab one word per lane, and parks each ballot word in shared
+// memory for the source lane. Either way the source lanes then act together: read
+// the value (search), write the tombstone (delete) or issue the 64-bit CAS of the
+// pair (replace), so the 32 CASes of a tile are in flight together and their
+// results are checked once. A claim that lost its race tries the following pair
+// of the same slab at once; ops that must follow a next pointer, or that ran off
+// their slab, restage just their slabs and go round again; a full list grows
+// through SlabAlloc (Sec. 5), by one batched allocation for all of a bulk-insert
+// tile's full lists.
 //
 // Staging just before serving (rather than a tile ahead into a second buffer)
 // keeps one 4 KB stage per warp, which leaves room for more resident warps, and
@@ -27,10 +30,13 @@
 // Search and delete batches do not restage inside a tile: an op that must go on
 // to its list's next slab waits in a per-warp ring and is served later in a
 // tile of such ops, 32 at a time, so one long list does not hold the whole warp
-// for another stage-and-match round. Insert and mixed batches serve each tile
-// to the end: their rounds also claim pairs and grow lists, and measured slower
-// when deferred. So do search and delete on tables much larger than L2 (the ones
-// whose slabs are pulled into L2 a tile ahead), where the ring measured slower.
+// for another stage-and-match round. Mixed batches sort each input tile's ops by
+// kind: inserts wait in a per-warp insert queue and are served as insert tiles,
+// searches and deletes go to the ring. Insert tiles are served to the end: their
+// rounds also claim pairs and grow lists, and measured slower when deferred. On
+// tables much larger than L2 (the ones whose slabs are pulled into L2 a tile
+// ahead) search and delete restage in the tile and mixed tiles hold all three
+// kinds side by side, which measured faster there.
 #pragma once
 #include "slab_device.cuh"
 #include "slab_wcws.cuh"
